@@ -1,0 +1,249 @@
+/*
+ * triot.h -- C ABI of the GB300 (sm_103a) TRIOT hot path.
+ *
+ * Joint iteration over dense row-major tensors of different shapes whose rank is known
+ * only at run time, with the index tuple visible to the operation: Heyl & Serang,
+ * "TRIOT: Faster tensor manipulation in C++11" (arXiv 1608.00099).  Three operations:
+ *   embed / crop  -- copy into a larger zero-padded tensor and back (Section 3,
+ *                    benchmark 1; Algorithm 13),
+ *   product       -- y[t] *= x[t] over the tuples shared by both shapes (Section 3,
+ *                    benchmark 2; apply_tensors of Algorithm 9),
+ *   moment        -- the tuple-weighted sum  m_i = sum_t p[t] * t_i  (Algorithms 10, 11).
+ *
+ * Conventions shared by every call
+ *   - Tensors are dense, contiguous and row-major.  Data pointers are DEVICE pointers
+ *     owned by the caller; 16-byte alignment is recommended (it enables 128-bit
+ *     accesses) but not required beyond the element size.
+ *   - Shapes are HOST arrays of `rank` int64 extents, read during the call only.
+ *     1 <= rank <= TRIOT_MAX_RANK.  Extents may be 0 (empty iteration) or 1.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *     enqueue work and return without synchronising; they allocate no memory, so they
+ *     may be captured in a CUDA graph.
+ *   - Every call returns a triot_status.  On failure nothing has been enqueued and
+ *     triot_last_error() describes the problem (thread-local string).
+ *   - dtype codes: TRIOT_F64, TRIOT_F32, TRIOT_BF16, TRIOT_F16.  IEEE round-to-nearest-
+ *     even throughout; denormals are kept (no flush to zero).
+ */
+#ifndef TRIOT_H
+#define TRIOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRIOT_MAX_RANK 24
+
+typedef enum triot_dtype {
+  TRIOT_F64 = 0,
+  TRIOT_F32 = 1,
+  TRIOT_BF16 = 2,
+  TRIOT_F16 = 3
+} triot_dtype;
+
+typedef enum triot_status {
+  TRIOT_OK = 0,
+  TRIOT_ERR_RANK = 1,      /* rank < 1 or rank > TRIOT_MAX_RANK                        */
+  TRIOT_ERR_SHAPE = 2,     /* negative extent, or a source not inside its target         */
+  TRIOT_ERR_NULL = 3,      /* a required pointer is NULL (data may be NULL when empty)   */
+  TRIOT_ERR_DTYPE = 4,     /* unknown dtype code                                         */
+  TRIOT_ERR_WORKSPACE = 5, /* workspace too small or misaligned                          */
+  TRIOT_ERR_ALIAS = 6,     /* x and y are the same pointer (they must not overlap)       */
+  TRIOT_ERR_CUDA = 7,      /* a CUDA runtime call or kernel launch failed                */
+  TRIOT_ERR_ARG = 8,       /* any other invalid argument (flags, sizes, tuning values)   */
+  TRIOT_ERR_DEVICE = 9     /* a device-side guard tripped (see triot_device_status)      */
+} triot_status;
+
+/* embed flag: y is already all zero; write only x's tuples (skip the pad). */
+#define TRIOT_EMBED_NOPAD 1u
+
+/* Thread-local description of the last failure of a call made by this thread. */
+const char* triot_last_error(void);
+/* Library version string, e.g. "triot-gb300 1.0 sm_103a". */
+const char* triot_version(void);
+
+/*
+ * triot_embed -- zero-padded copy at the origin.
+ *   Section 3 benchmark 1 run in reverse (the abstract's "copying data from one tensor to
+ *   another larger, zero padded tensor"): for every tuple t of y's shape,
+ *       y[t] = x[t]  if t_i < xshape[i] for all i,   y[t] = +0.0 (all bits zero) otherwise.
+ *   Requires xshape[i] <= yshape[i] for every i (else TRIOT_ERR_SHAPE), the bounds check
+ *   check_tensor_pack_bounds performs once per call (Algorithm 8).
+ *   x: device, rank-`rank` tensor of xshape, read only.  y: device tensor of yshape,
+ *   written in full (with TRIOT_EMBED_NOPAD only x's tuples are written).
+ *   The operation moves bits: it is bit-exact for every dtype (the dtype only fixes the
+ *   element size).  x and y must not overlap.
+ */
+int triot_embed(int rank, const int64_t* xshape, const void* x, const int64_t* yshape,
+                void* y, int dtype, unsigned flags, void* stream);
+
+/*
+ * triot_crop -- the inverse of embed (Algorithm 13, benchmark 1):
+ *       x[t] = y[t]  for every tuple t of x's shape.
+ *   Requires xshape[i] <= yshape[i].  x (device, written in full) and y (device, read)
+ *   must not overlap.  Bit-exact for every dtype.
+ */
+int triot_crop(int rank, const int64_t* xshape, void* x, const int64_t* yshape,
+               const void* y, int dtype, void* stream);
+
+/*
+ * triot_product -- in-place element-wise product over the shape intersection:
+ *       y[t] = y[t] * x[t]  for every tuple t with t_i < min(xshape[i], yshape[i]);
+ *   y elsewhere is untouched (Section 3 benchmark 2 visits "only tuple indices shared by
+ *   both"; the write goes to the destination only, as apply_tensors in Algorithm 9).
+ *   f64/f32: one IEEE multiply.  bf16/f16: the exact product of the stored values,
+ *   rounded once to the storage type.  x (device, read) and y (device, read-write) must
+ *   not overlap (the __restrict contract of Section 4).
+ */
+int triot_product(int rank, const int64_t* xshape, const void* x, const int64_t* yshape,
+                  void* y, int dtype, void* stream);
+
+/*
+ * triot_moment_workspace_size -- bytes of device workspace triot_moment needs for this
+ *   shape and dtype (per-block partial sums).  Writes *bytes; never fails for valid
+ *   arguments.  The size depends only on (rank, shape, dtype) and the tuning in force.
+ */
+int triot_moment_workspace_size(int rank, const int64_t* shape, int dtype, size_t* bytes);
+
+/*
+ * triot_moment -- tuple-weighted first moments (Algorithm 11 with one weight tensor,
+ *   the tuple made visible as in Algorithm 10; tuples are zero-based):
+ *       out[i]    = sum over tuples t of shape  p[t] * t_i     (i = 0 .. rank-1)
+ *       out[rank] = sum over tuples t of shape  p[t]            (the mass)
+ *   p: device tensor, read only.  out: DEVICE array of rank+1 doubles, written.
+ *   workspace: device scratch of at least triot_moment_workspace_size() bytes, 16-byte
+ *   aligned, owned by the caller; its contents on entry are ignored.
+ *   Accumulation: f64 input in exact fixed point (one rounding to f64 per block and one
+ *   at the end); f32/bf16/f16 input in compensated f32 per thread.  Block partials are
+ *   combined by a second kernel in exact fixed point, so results are bit-identical from
+ *   run to run.  Two kernels are enqueued on `stream`.
+ */
+int triot_moment(int rank, const int64_t* shape, const void* p, int dtype, double* out,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------ batched launch */
+
+/*
+ * One pair of the batched pipeline: x (xshape) is embedded at the origin of a zero-padded
+ * y (yshape), then y[t] *= x[t] over x's shape, then the moment of y is written to
+ * moment_out[0 .. rank] (rank moments then the mass, as triot_moment).  All pointers are
+ * device pointers owned by the caller.  Section 4: independent problems are partitioned
+ * across processors with no shared state.
+ */
+typedef struct triot_batch_desc {
+  int rank;                           /* 1 .. TRIOT_MAX_RANK                         */
+  int64_t xshape[TRIOT_MAX_RANK];
+  int64_t yshape[TRIOT_MAX_RANK];
+  const void* x;                      /* device, read                                 */
+  void* y;                            /* device, written in full                      */
+  double* moment_out;                 /* device, rank + 1 doubles                     */
+} triot_batch_desc;
+
+/* Launch geometry of a kernel family; zero fields mean "use the tuned or default value". */
+typedef struct triot_tune {
+  int threads;      /* threads per CTA (multiple of 32, 64 .. 1024)                       */
+  int tile_elems;   /* elements of the iteration space one CTA handles per tile          */
+  int ctas_per_sm;  /* resident CTAs per SM for persistent launches (1 .. 8)              */
+  int unroll;       /* vectors in flight per thread (1 .. 8)                              */
+} triot_tune;
+
+typedef struct triot_plan triot_plan;
+
+/* batch plan modes */
+#define TRIOT_BATCH_FUSED 0       /* one persistent kernel: embed+product+moment per tile */
+#define TRIOT_BATCH_PHASED 1      /* persistent embed, product, moment phases            */
+
+/*
+ * triot_batch_plan_create -- validate `n` descriptors (all of one dtype: TRIOT_F32,
+ *   TRIOT_F64, TRIOT_BF16 or TRIOT_F16), build the device work list (descriptors, tile
+ *   prefix sums, moment slots) and return an opaque plan.  This call allocates device
+ *   memory (once); running the plan does not.  `tune` may be NULL.  Rejects descriptors
+ *   whose x is not inside y, ranks out of range or NULL pointers (TRIOT_ERR_*; nothing
+ *   is allocated then).
+ */
+int triot_batch_plan_create(const triot_batch_desc* descs, int n, int dtype, int mode,
+                            const triot_tune* tune, triot_plan** out);
+/*
+ * triot_batch_run -- run the whole batch on `stream`.  The first run on a given stream
+ *   captures the launch sequence into a CUDA graph; later runs replay it with one
+ *   cudaGraphLaunch.  Pair buffers are read and written in place.
+ */
+int triot_batch_run(triot_plan* plan, void* stream);
+/* Run the same work as plain per-pair launches (embed, product, moment per pair). */
+int triot_batch_run_plain(triot_plan* plan, void* stream);
+/* Bytes of device memory the plan holds, and its tile count. */
+int triot_batch_plan_info(const triot_plan* plan, size_t* device_bytes, int64_t* tiles);
+int triot_batch_plan_destroy(triot_plan* plan);
+
+/* ------------------------------------------------------------------ tuning */
+
+/* op codes for the tuning calls */
+#define TRIOT_OP_EMBED 0
+#define TRIOT_OP_CROP 1
+#define TRIOT_OP_PRODUCT 2
+#define TRIOT_OP_MOMENT 3
+#define TRIOT_OP_BATCH 4
+
+/*
+ * triot_autotune -- time candidate launch geometries for one (op, rank, shapes, dtype)
+ *   on the caller's buffers (which it overwrites exactly as the op would) with CUDA
+ *   events on `stream`, keep the fastest in the in-process cache (keyed by GPU, op,
+ *   dtype, effective rank and inner-extent class) and return it in *best.  For
+ *   TRIOT_OP_MOMENT pass p as `x`, NULL as `y`, and a workspace large enough for every
+ *   candidate (triot_moment_workspace_size with the largest geometry: use
+ *   TRIOT_MOMENT_MAX_WORKSPACE_PER_RANK * (rank + 1) bytes).  Synchronises `stream`.
+ */
+#define TRIOT_MOMENT_MAX_WORKSPACE_PER_RANK (16384 * 8)
+int triot_autotune(int op, int rank, const int64_t* xshape, const void* x,
+                   const int64_t* yshape, void* y, int dtype, void* workspace,
+                   size_t workspace_bytes, void* stream, triot_tune* best);
+/* Read / force the cached geometry for the key of these arguments (no GPU work). */
+int triot_tune_get(int op, int rank, const int64_t* xshape, const int64_t* yshape, int dtype,
+                   triot_tune* out);
+int triot_tune_set(int op, int rank, const int64_t* xshape, const int64_t* yshape, int dtype,
+                   const triot_tune* tune);
+/* Persist / restore the cache as JSON (one object per key).  Load merges entries. */
+int triot_tune_save(const char* path);
+int triot_tune_load(const char* path);
+int triot_tune_clear(void);
+
+/* ------------------------------------------------------------------ introspection */
+
+/*
+ * triot_canonicalize -- host only, no GPU work.  Shows how a call's shapes are reduced
+ *   before launch: unit axes dropped (Section 4: trivial axes "can simply be ignored")
+ *   and neighbouring axes merged where both tensors are contiguous across them (and, for
+ *   embed, x is full along the inner one).  op: TRIOT_OP_EMBED / CROP / PRODUCT / MOMENT;
+ *   yshape is ignored (may be NULL) for TRIOT_OP_MOMENT.  Writes the effective rank to
+ *   *eff_rank and per effective axis (outermost first; arrays of TRIOT_MAX_RANK):
+ *     ext     iteration extent (embed: y's, crop: x's, product: the intersection's,
+ *             moment: p's),
+ *     xstride x's stride in elements along the axis (moment: 0),
+ *     ystride y's stride in elements (moment: 0),
+ *     xbound  embed: x's extent along the axis (other ops: ext),
+ *     orig    the first original axis merged into the axis (moment: its original axis).
+ *   Any output pointer but eff_rank and ext may be NULL.
+ */
+int triot_canonicalize(int op, int rank, const int64_t* xshape, const int64_t* yshape,
+                       int* eff_rank, int64_t* ext, int64_t* xstride, int64_t* ystride,
+                       int64_t* xbound, int* orig);
+
+/*
+ * triot_fastdiv_check -- host only.  Runs the magic-multiplier division used by the
+ *   kernels' flat-to-tuple decode (Granlund & Montgomery, "Division by invariant integers
+ *   using multiplication", PLDI 1994) on `count` 32-bit dividends n[k] for divisor d
+ *   (1 <= d < 2^31) and writes quotients q[k] and remainders r[k].  For tests.
+ */
+int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q, uint32_t* r);
+
+/* Sticky device-side status (TRIOT_OK or TRIOT_ERR_DEVICE) of the current device; reading
+ * it synchronises the device and clears it. */
+int triot_device_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRIOT_H */

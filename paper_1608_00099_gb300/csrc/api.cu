@@ -1,0 +1,281 @@
+// C ABI of the TRIOT hot path: validation, canonicalisation, per-rank dispatch, launch.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/triot.h"
+#include "internal.h"
+#include "kernels.h"
+#include "plan.h"
+
+namespace triot {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int ok() { return TRIOT_OK; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  return fail(TRIOT_ERR_CUDA, buf);
+}
+
+// ------------------------------------------------------------------ devices
+int device_info(DeviceInfo& out) {
+  static std::mutex mu;
+  static std::vector<DeviceInfo> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(mu);
+  for (const auto& d : cache)
+    if (d.device == dev) { out = d; return TRIOT_OK; }
+  DeviceInfo d;
+  d.device = dev;
+  e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  snprintf(d.name, sizeof d.name, "%s", prop.name);
+  cache.push_back(d);
+  out = d;
+  return TRIOT_OK;
+}
+
+bool valid_dtype(int dt) { return dt >= TRIOT_F64 && dt <= TRIOT_F16; }
+
+bool overlaps_bytes(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+static int64_t count(int rank, const int64_t* s) {
+  int64_t n = 1;
+  for (int i = 0; i < rank; ++i) n *= s[i];
+  return n;
+}
+
+// ------------------------------------------------------------------ row ops
+int launch_rows(int op, int rank, const int64_t* xshape, const void* x, const int64_t* yshape,
+                const void* y, int dtype, unsigned flags, cudaStream_t stream,
+                const TuneCfg* force) {
+  if (!valid_dtype(dtype)) return fail(TRIOT_ERR_DTYPE, "unknown dtype code");
+  if (op == ROW_EMBED && (flags & ~TRIOT_EMBED_NOPAD)) return fail(TRIOT_ERR_ARG, "unknown embed flag");
+  Canon c;
+  bool x_empty = false;
+  std::string err;
+  int st = canon_rows(op, rank, xshape, yshape, c, x_empty, err);
+  if (st) return fail(st, err);
+  const int es = dtype_size(dtype);
+  const int64_t nx = count(rank, xshape), ny = count(rank, yshape);
+  // embed writes all of y even when x is empty
+  const bool work = (op == ROW_EMBED) ? (ny > 0) : !c.empty;
+  if (!work) return ok();
+  if ((op != ROW_EMBED || nx > 0) && !x) return fail(TRIOT_ERR_NULL, "x is NULL");
+  if (!y) return fail(TRIOT_ERR_NULL, "y is NULL");
+  if (x && nx > 0 && overlaps_bytes(x, size_t(nx) * es, y, size_t(ny) * es))
+    return fail(TRIOT_ERR_ALIAS, "x and y overlap");
+  DeviceInfo dev;
+  if ((st = device_info(dev))) return st;
+  TuneCfg t = force ? *force : tune_lookup(op == ROW_EMBED ? TRIOT_OP_EMBED : op == ROW_CROP ? TRIOT_OP_CROP : TRIOT_OP_PRODUCT,
+                                           dtype, c);
+  // A = written tensor, B = read tensor
+  const void* A = (op == ROW_CROP) ? x : y;
+  const void* B = (op == ROW_CROP) ? y : x;
+  RowLaunch L;
+  plan_rows(op, c, x_empty, es, A, B, flags, t, dev, L);
+  const void* fn = (op == ROW_EMBED) ? embed_kernel_ptr(es, L.g.nouter)
+                   : (op == ROW_CROP) ? crop_kernel_ptr(es, L.g.nouter)
+                                      : product_kernel_ptr(dtype, L.g.nouter);
+  if (!fn) return fail(TRIOT_ERR_RANK, "no kernel for this effective rank");
+  if (L.block < 32 || L.block > 1024 || L.block % 32) return fail(TRIOT_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+  // an empty x leaves B unused; give the kernel a valid (never dereferenced) pointer
+  const void* Bk = B ? B : A;
+  void* args[] = {(void*)&L.g, (void*)&A, (void*)&Bk};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.block), args, L.smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "row kernel launch");
+  return ok();
+}
+
+// ------------------------------------------------------------------ moment
+static int moment_occupancy(int dtype, int D, int& occ) {
+  static std::mutex mu;
+  static int table[4][kMaxRank + 1] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (!table[dtype][D]) {
+    const void* fn = moment_kernel_ptr(dtype, D);
+    int o = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kMomentWarps * 32, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    table[dtype][D] = o > 0 ? o : 1;
+  }
+  occ = table[dtype][D];
+  return TRIOT_OK;
+}
+
+int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, const TuneCfg* force,
+                     MomentLaunch& L) {
+  if (!valid_dtype(dtype)) return fail(TRIOT_ERR_DTYPE, "unknown dtype code");
+  Canon c;
+  std::string err;
+  int st = canon_moment(rank, shape, c, err);
+  if (st) return fail(st, err);
+  DeviceInfo dev;
+  if ((st = device_info(dev))) return st;
+  int occ = 1;
+  if ((st = moment_occupancy(dtype, c.D, occ))) return st;
+  TuneCfg t = force ? *force : tune_lookup(TRIOT_OP_MOMENT, dtype, c);
+  plan_moment(c, rank, dtype_size(dtype), p, t, dev, occ, L);
+  if (L.grid > kMaxMomentParts) return fail(TRIOT_ERR_ARG, "moment grid exceeds the partial limit");
+  return TRIOT_OK;
+}
+
+size_t moment_ws_bytes(const MomentLaunch& L) {
+  const size_t b = size_t(L.grid) * size_t(L.g.D + 1) * sizeof(double);
+  return b < 16 ? 16 : b;
+}
+
+int launch_moment(const MomentLaunch& L, int dtype, const void* p, double* out, void* ws,
+                  cudaStream_t stream) {
+  cudaError_t e;
+  if (!L.empty) {
+    const void* fn = moment_kernel_ptr(dtype, L.g.D);
+    if (!fn) return fail(TRIOT_ERR_RANK, "no moment kernel for this effective rank");
+    double* part = static_cast<double*>(ws);
+    void* args[] = {(void*)&L.g, (void*)&p, (void*)&part};
+    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(kMomentWarps * 32), args, 0, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moment kernel launch");
+  }
+  const double* partc = static_cast<const double*>(ws);
+  void* cargs[] = {(void*)&L.cg, (void*)&partc, (void*)&out};
+  e = cudaLaunchKernel(combine_kernel_ptr(), dim3(L.g.D + 1), dim3(kCombineThreadsHost), cargs, 0, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "combine kernel launch");
+  return ok();
+}
+
+int moment_call(int rank, const int64_t* shape, const void* p, int dtype, double* out, void* ws,
+                size_t ws_bytes, cudaStream_t stream, const TuneCfg* force) {
+  MomentLaunch L;
+  int st = plan_moment_call(rank, shape, dtype, p, force, L);
+  if (st) return st;
+  if (!out) return fail(TRIOT_ERR_NULL, "out is NULL");
+  if (!L.empty && !p) return fail(TRIOT_ERR_NULL, "p is NULL");
+  if (!ws) return fail(TRIOT_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return fail(TRIOT_ERR_WORKSPACE, "workspace is not 16-byte aligned");
+  if (ws_bytes < moment_ws_bytes(L)) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, moment_ws_bytes(L));
+    return fail(TRIOT_ERR_WORKSPACE, buf);
+  }
+  return launch_moment(L, dtype, p, out, ws, stream);
+}
+
+}  // namespace triot
+
+using namespace triot;
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char* triot_last_error(void) { return g_err.c_str(); }
+
+const char* triot_version(void) { return "triot-gb300 1.0 sm_103a"; }
+
+int triot_embed(int rank, const int64_t* xshape, const void* x, const int64_t* yshape, void* y,
+                int dtype, unsigned flags, void* stream) {
+  return launch_rows(ROW_EMBED, rank, xshape, x, yshape, y, dtype, flags, (cudaStream_t)stream, nullptr);
+}
+
+int triot_crop(int rank, const int64_t* xshape, void* x, const int64_t* yshape, const void* y,
+               int dtype, void* stream) {
+  // crop writes x: pass x as the written tensor through the same launcher
+  return launch_rows(ROW_CROP, rank, xshape, x, yshape, y, dtype, 0, (cudaStream_t)stream, nullptr);
+}
+
+int triot_product(int rank, const int64_t* xshape, const void* x, const int64_t* yshape, void* y,
+                  int dtype, void* stream) {
+  return launch_rows(ROW_PRODUCT, rank, xshape, x, yshape, y, dtype, 0, (cudaStream_t)stream, nullptr);
+}
+
+int triot_moment_workspace_size(int rank, const int64_t* shape, int dtype, size_t* bytes) {
+  if (!bytes) return fail(TRIOT_ERR_NULL, "bytes is NULL");
+  MomentLaunch L;
+  int st = plan_moment_call(rank, shape, dtype, nullptr, nullptr, L);
+  if (st) return st;
+  *bytes = moment_ws_bytes(L);
+  return ok();
+}
+
+int triot_moment(int rank, const int64_t* shape, const void* p, int dtype, double* out,
+                 void* workspace, size_t workspace_bytes, void* stream) {
+  return moment_call(rank, shape, p, dtype, out, workspace, workspace_bytes, (cudaStream_t)stream, nullptr);
+}
+
+int triot_canonicalize(int op, int rank, const int64_t* xshape, const int64_t* yshape, int* eff_rank,
+                       int64_t* ext, int64_t* xstride, int64_t* ystride, int64_t* xbound, int* orig) {
+  if (!eff_rank || !ext) return fail(TRIOT_ERR_NULL, "output pointer is NULL");
+  Canon c;
+  std::string err;
+  int st;
+  if (op == TRIOT_OP_MOMENT) {
+    st = canon_moment(rank, xshape, c, err);
+    if (st) return fail(st, err);
+    *eff_rank = c.D;
+    for (int i = 0; i < c.D; ++i) {
+      ext[i] = c.ext[i];
+      if (xstride) xstride[i] = 0;
+      if (ystride) ystride[i] = 0;
+      if (xbound) xbound[i] = c.ext[i];
+      if (orig) orig[i] = c.orig[i];
+    }
+    return ok();
+  }
+  const int rop = op == TRIOT_OP_EMBED ? ROW_EMBED : op == TRIOT_OP_CROP ? ROW_CROP : op == TRIOT_OP_PRODUCT ? ROW_PRODUCT : -1;
+  if (rop < 0) return fail(TRIOT_ERR_ARG, "unknown op");
+  bool x_empty = false;
+  st = canon_rows(rop, rank, xshape, yshape, c, x_empty, err);
+  if (st) return fail(st, err);
+  *eff_rank = c.D;
+  // A is the written tensor (y for embed/product, x for crop), B the read one
+  for (int i = 0; i < c.D; ++i) {
+    ext[i] = c.ext[i];
+    if (xstride) xstride[i] = (rop == ROW_CROP) ? c.sa[i] : c.sb[i];
+    if (ystride) ystride[i] = (rop == ROW_CROP) ? c.sb[i] : c.sa[i];
+    if (xbound) xbound[i] = c.bound[i];
+    if (orig) orig[i] = c.orig[i];
+  }
+  return ok();
+}
+
+int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q, uint32_t* r) {
+  if (d == 0) return fail(TRIOT_ERR_ARG, "divisor is zero");
+  if (count && (!n || !q || !r)) return fail(TRIOT_ERR_NULL, "array pointer is NULL");
+  const FastDiv f = make_fastdiv(d);
+  for (size_t k = 0; k < count; ++k) {
+    uint32_t rr;
+    q[k] = fdivmod(n[k], f, rr);
+    r[k] = rr;
+  }
+  return ok();
+}
+
+int triot_device_status(void) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  int flag = 0;
+  st_read_device_flag(&flag);
+  return flag ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped") : ok();
+}
+
+}  // extern "C"

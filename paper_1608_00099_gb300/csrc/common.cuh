@@ -1,0 +1,95 @@
+// Internal definitions shared by the host planner and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fastdiv.cuh"
+
+namespace triot {
+
+constexpr int kMaxRank = 24;
+constexpr int kMomentWarps = 4;  // warps per CTA of the moment kernels
+
+enum RowOp { ROW_EMBED = 0, ROW_CROP = 1, ROW_PRODUCT = 2 };
+
+// Element types of the kernels.
+enum Dtype { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, DT_F16 = 3 };
+
+inline int dtype_size(int dt) { return dt == DT_F64 ? 8 : dt == DT_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------------ canonical form
+//
+// A call's shapes reduced for launch (Section 4: trivial axes are ignored; adjacent axes
+// that are contiguous in every tensor behave as one axis).  Axes are listed outermost
+// first.  Strides are in elements.  For embed the iteration space is y and `bound` holds
+// x's extent per axis; for crop it is x; for product it is the intersection I; for the
+// moment it is p (no merging: every axis has its own output).
+struct Canon {
+  int D = 0;                       // effective rank, >= 1
+  int64_t ext[kMaxRank];           // iteration extents
+  int64_t sa[kMaxRank];            // strides of tensor A (the written tensor)
+  int64_t sb[kMaxRank];            // strides of tensor B (the read tensor)
+  int64_t bound[kMaxRank];         // embed: x's extent per axis
+  int orig[kMaxRank];              // moment: original axis of each effective axis
+  int64_t total = 0;               // number of iterated elements
+  bool empty = false;              // some iteration extent is zero
+};
+
+// ------------------------------------------------------------------ row kernels
+//
+// The iteration space is viewed as `rows` rows of `inner` contiguous elements; a row is a
+// tuple of the outer axes.  Outer-axis data is stored innermost first: entry k describes
+// canonical axis D-2-k.  A tile is either a run of whole rows or one segment of a row.
+struct RowInfo {
+  long long a;   // offset of the row in A
+  long long b;   // offset of the row in B, or -1 (embed: row outside x)
+};
+
+struct RowGeom {
+  int nouter;                      // outer axes (D - 1)
+  int path;                        // PATH_* below, uniform for the launch
+  FastDiv div[kMaxRank];           // outer extents (innermost first) for the decode
+  long long ext[kMaxRank];         // outer extents (innermost first)
+  long long sa[kMaxRank];          // A strides per outer axis
+  long long sb[kMaxRank];          // B strides per outer axis
+  long long bound[kMaxRank];       // embed: x extent per outer axis
+  long long rows;                  // number of rows
+  long long inner;                 // row length (iteration)
+  long long b_inner;               // embed: x's extent of the inner axis
+  long long rows_per_tile;         // multi-row tiles
+  long long segs_per_row;          // > 1: a tile is one segment of a row
+  long long seg_len;               // segment length (multiple of the vector width)
+  long long ntiles;
+  FastDiv inner_div;               // divisor = inner (only when inner < 2^31)
+  FastDiv seg_div;                 // divisor = segs_per_row
+  int rows32;                      // rows fit the 32-bit decode
+  int nopad;                       // embed: skip writing the pad
+};
+
+enum {
+  PATH_VEC = 0,   // vector slots inside one row; B loaded as a vector
+  PATH_ROW = 1,   // vector slots inside one row; B loaded per element
+  PATH_GEN = 2    // one element at a time (any row length, any alignment)
+};
+
+// ------------------------------------------------------------------ moment
+struct MomentGeom {
+  int D;                           // effective rank
+  int nchunks;                     // chunks per lane segment
+  long long n;                     // elements
+  long long seg;                   // lane segment length S (multiple of the chunk)
+  long long nwarpseg;              // warp segments (32 lane segments each)
+  int n32;                         // n < 2^32: 32-bit decode
+  int aligned;                     // p is 16-byte aligned: cp.async staging
+  FastDiv div[kMaxRank];           // extents (axis order, outermost first)
+  long long ext[kMaxRank];         // extents (axis order, outermost first)
+};
+
+struct CombineGeom {
+  int D;                           // effective rank
+  int rank;                        // caller's rank (output length rank + 1)
+  int nparts;                      // partial vectors in the workspace
+  int orig[kMaxRank];              // output index of each effective axis
+};
+
+}  // namespace triot

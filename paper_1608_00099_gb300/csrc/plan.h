@@ -1,0 +1,54 @@
+// Host planning: argument validation, shape canonicalisation and launch geometry.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+
+#include "common.cuh"
+
+namespace triot {
+
+// Launch knobs of one kernel family; 0 = default.
+struct TuneCfg {
+  int threads = 0;
+  int tile_elems = 0;
+  int ctas_per_sm = 0;
+  int unroll = 0;
+};
+
+struct DeviceInfo {
+  int device = 0;
+  int sms = 152;
+  char name[128] = {0};
+};
+
+// Validate and canonicalise a row operation (ROW_EMBED / ROW_CROP / ROW_PRODUCT).
+// Returns a triot_status code; on error `err` says why.
+int canon_rows(int op, int rank, const int64_t* xshape, const int64_t* yshape, Canon& c,
+               bool& x_empty, std::string& err);
+// Validate and canonicalise a moment (drop extent-1 axes, keep the axis map).
+int canon_moment(int rank, const int64_t* shape, Canon& c, std::string& err);
+
+// Launch geometry of a row kernel.  `es` is the element size in bytes.
+struct RowLaunch {
+  RowGeom g;
+  int grid = 0, block = 0;
+  size_t smem = 0;
+};
+void plan_rows(int op, const Canon& c, bool x_empty, int es, const void* A, const void* B,
+               unsigned flags, const TuneCfg& t, const DeviceInfo& dev, RowLaunch& L);
+
+struct MomentLaunch {
+  MomentGeom g;
+  CombineGeom cg;
+  int grid = 0;        // CTAs of the moment kernel (= number of partial vectors)
+  bool empty = false;  // nothing to sum: only the combine runs (it writes zeros)
+};
+// `occ` = resident CTAs per SM of the chosen kernel (from the occupancy calculator).
+void plan_moment(const Canon& c, int rank, int es, const void* p, const TuneCfg& t,
+                 const DeviceInfo& dev, int occ, MomentLaunch& L);
+
+// lane segment length chosen for the moment (exposed for the workspace bound)
+long long moment_segment(const Canon& c, int es, long long target_lanes);
+
+}  // namespace triot
