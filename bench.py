@@ -1,0 +1,444 @@
+"""Benchmark of the TRIOT hot path on GB300: effective HBM GB/s per op and for a whole step.
+
+A step is one pass of the path over the f64 d=8 workload: embed x (9^8, U(0,1)) into a
+zero-padded y of shape (11,10)x4, y'[t] *= x[t] over the intersection with a U(0,1) y'
+of shape (12,8)x4, and the tuple-weighted moment of p = x / sum(x) (with the mass).
+`value` is the algorithmic bytes of those three ops divided by the device time of K
+steps (inputs resident in HBM, every buffer larger than L2).  The JSON line also
+carries per-op GB/s, the roofline of the dominant kernel (embed), an end-to-end figure
+through the same C ABI with pinned host buffers copied in and out every step, SM clocks
+sampled during the run, the CPU oracle timed on the host cores, and the batched
+workload (4096 f32 pairs: one persistent graph launch vs per-pair plain launches).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+NOMINAL_HBM_GBS = 8000.0
+WORKLOAD = "f64_d8"
+WORKLOAD_DESC = ("f64 d=8: embed x 9^8 U(0,1) -> (11,10)x4; product y*=x over (9,8)x4 into U(0,1) "
+                 "(12,8)x4; moment of x/sum(x)")
+METRIC = "effective HBM GB/s (frac of 8 TB/s) per op; batched vs plain launch elem/s"
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def step_bytes(cfg):
+    nx = int(np.prod(cfg.xshape))
+    ny = int(np.prod(cfg.embed_shape))
+    I = int(np.prod([min(a, b) for a, b in zip(cfg.xshape, cfg.prod_shape)]))
+    return {"embed": 8 * (nx + ny), "product": 3 * 8 * I, "moment": 8 * nx}
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    import torch
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend=backend)
+    return rank, ws, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v: float, device=None) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        busy = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local, dist):
+    import torch
+
+    from paper_1608_00099_gb300 import build as tb
+    from paper_1608_00099_gb300 import synth, triot
+
+    tb.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.config_f64_d8()
+    xh = cfg.x_values()
+    yph = cfg.yprod_values()
+    ph = synth.normalise(xh)
+    x = torch.from_numpy(xh.reshape(cfg.xshape)).to(dev)
+    y1 = torch.empty(cfg.embed_shape, dtype=torch.float64, device=dev)
+    y2 = torch.from_numpy(yph.reshape(cfg.prod_shape)).to(dev)
+    p = torch.from_numpy(ph.reshape(cfg.xshape)).to(dev)
+    out = torch.empty(len(cfg.xshape) + 1, dtype=torch.float64, device=dev)
+    ws = torch.empty(triot.triot_moment_workspace_size(cfg.xshape, torch.float64) // 8 + 2,
+                     dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    b = step_bytes(cfg)
+    step_total = sum(b.values())
+
+    def step():
+        triot.triot_embed(x, y1, stream=stream)
+        triot.triot_product(x, y2, stream=stream)
+        triot.triot_moment(p, out=out, workspace=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # per-op events inside the timed region (recorded on the launching stream)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    # a short soak at the same work so the clock sampler sees the GPU under load
+    t_soak = time.time()
+    while time.time() - t_soak < args.soak:
+        for _ in range(50):
+            step()
+        torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(args.steps):
+        e = evs[k]
+        e[0].record(stream)
+        triot.triot_embed(x, y1, stream=stream)
+        e[1].record(stream)
+        triot.triot_product(x, y2, stream=stream)
+        e[2].record(stream)
+        triot.triot_moment(p, out=out, workspace=ws, stream=stream)
+        e[3].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop() if sampler else None
+    ms = start.elapsed_time(stop)
+    ms_max = max_over_ranks(dist, ms, dev)
+    op_ms = {"embed": 0.0, "product": 0.0, "moment": 0.0}
+    for e in evs:
+        op_ms["embed"] += e[0].elapsed_time(e[1])
+        op_ms["product"] += e[1].elapsed_time(e[2])
+        op_ms["moment"] += e[2].elapsed_time(e[3])
+    K = args.steps
+    value = step_total * K * world / (ms_max * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    ops = {}
+    for name, tot in op_ms.items():
+        gbs = b[name] / (tot / K * 1e-3) / 1e9
+        ops[name] = {"gbs": round(gbs, 1), "us": round(tot / K * 1e3, 2), "bytes": b[name],
+                     "frac_8tbs": round(gbs / NOMINAL_HBM_GBS, 4), "frac_measured": round(gbs / peak, 4)}
+    emb = ops["embed"]
+    traffic = ncu_traffic("embed_f64_d8")
+    roofline = {"bound": "hbm", "kernel": "rows_kernel<embed, f64, 7 outer axes>",
+                "achieved": emb["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": round(emb["gbs"] / peak, 4), "peak_kind": peak_kind, "traffic": traffic}
+
+    # end to end: pinned host buffers in, results out, every step through the same C ABI
+    e2e = run_e2e(args, triot, cfg, xh, yph, ph, dev, stream, step_total)
+
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / K, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (SplitMix64 seed 1002, U(0,1)); replicas only across GPUs",
+        "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "bytes_per_step": step_total,
+                   "frac_8tbs": round(value / world / NOMINAL_HBM_GBS, 4),
+                   "l2": "every buffer is larger than L2 (smallest: x, 344 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "ops": ops, "roofline": roofline, "e2e": e2e, "gpu_launches": 4 * K,
+        "clocks": clocks,
+    }
+    if not args.no_batch:
+        result["batch"] = run_batch(args, triot, synth, dev, stream)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(args, cfg, xh, yph, ph)
+    return result
+
+
+def ncu_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{name}.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in rec.get("sources", []):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != rec.get("sources_sha256"):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_e2e(args, triot, cfg, xh, yph, ph, dev, stream, step_total):
+    import torch
+    K = max(3, min(args.steps, args.e2e_steps))
+    xp = torch.from_numpy(xh.reshape(cfg.xshape)).pin_memory()
+    yp = torch.from_numpy(yph.reshape(cfg.prod_shape)).pin_memory()
+    pp = torch.from_numpy(ph.reshape(cfg.xshape)).pin_memory()
+    y1h = torch.empty(cfg.embed_shape, dtype=torch.float64).pin_memory()
+    y2h = torch.empty(cfg.prod_shape, dtype=torch.float64).pin_memory()
+    mh = torch.empty(len(cfg.xshape) + 1, dtype=torch.float64).pin_memory()
+    x = torch.empty(cfg.xshape, dtype=torch.float64, device=dev)
+    y1 = torch.empty(cfg.embed_shape, dtype=torch.float64, device=dev)
+    y2 = torch.empty(cfg.prod_shape, dtype=torch.float64, device=dev)
+    p = torch.empty(cfg.xshape, dtype=torch.float64, device=dev)
+    out = torch.empty(len(cfg.xshape) + 1, dtype=torch.float64, device=dev)
+    ws = torch.empty(triot.triot_moment_workspace_size(cfg.xshape, torch.float64) // 8 + 2,
+                     dtype=torch.float64, device=dev)
+
+    def step():
+        x.copy_(xp, non_blocking=True)
+        y2.copy_(yp, non_blocking=True)
+        p.copy_(pp, non_blocking=True)
+        triot.triot_embed(x, y1, stream=stream)
+        triot.triot_product(x, y2, stream=stream)
+        triot.triot_moment(p, out=out, workspace=ws, stream=stream)
+        y1h.copy_(y1, non_blocking=True)
+        y2h.copy_(y2, non_blocking=True)
+        mh.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = 8 * (xp.numel() + yp.numel() + pp.numel())
+    d2h = 8 * (y1h.numel() + y2h.numel() + mh.numel())
+    return {"value": round(step_total * K / dt / 1e9, 1), "unit": "GB/s", "steps": K,
+            "ms_per_step": round(dt / K * 1e3, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def run_batch(args, triot, synth, dev, stream):
+    """4096 f32 pairs: fused persistent graph launch, phased persistent, plain launches."""
+    import torch
+    pairs = synth.config_batch_shapes()
+    xs_h = synth.batch_x_values(pairs)
+    xs = [torch.from_numpy(v.astype(np.float32).reshape(pr.xshape)).to(dev) for pr, v in zip(pairs, xs_h)]
+    ys = [torch.empty(pr.yshape, dtype=torch.float32, device=dev) for pr in pairs]
+    outs = [torch.zeros(len(pr.xshape) + 1, dtype=torch.float64, device=dev) for pr in pairs]
+    ny = sum(int(np.prod(pr.yshape)) for pr in pairs)
+    nx = sum(int(np.prod(pr.xshape)) for pr in pairs)
+    fused = triot.BatchPlan(xs, ys, outs, mode=triot.BATCH_FUSED)
+    phased = triot.BatchPlan(xs, ys, outs, mode=triot.BATCH_PHASED)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    res = {"workload": "4096 f32 pairs, rank U{2..10}, extents U{2..32}, |y| <= 2^22",
+           "elements_y": ny, "elements_x": nx}
+    ms_f = timed(lambda: fused.run(stream), args.batch_reps)
+    ms_p = timed(lambda: phased.run(stream), args.batch_reps)
+    ms_plain = timed(lambda: fused.run_plain(stream), max(2, args.batch_reps // 5))
+    # the same plain launches captured in one CUDA graph (separates launch overhead)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        fused.run_plain(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            fused.run_plain(torch.cuda.current_stream())
+    ms_pg = timed(lambda: g.replay(), max(2, args.batch_reps // 2))
+    fused_bytes = 4 * (nx + ny)
+    for name, ms in (("fused_graph", ms_f), ("phased_graph", ms_p), ("plain_launches", ms_plain),
+                     ("plain_in_graph", ms_pg)):
+        res[name] = {"ms": round(ms, 3), "elem_per_s": round(ny / (ms * 1e-3), 1),
+                     "gbs_fused_bytes": round(fused_bytes / (ms * 1e-3) / 1e9, 1)}
+    res["launches"] = {"fused_graph": 2, "phased_graph": 4, "plain_launches": 4 * len(pairs)}
+    res["speedup_fused_vs_plain"] = round(ms_plain / ms_f, 2)
+    fused.close()
+    phased.close()
+    return res
+
+
+# ------------------------------------------------------------------ the oracle on the host
+
+def oracle_step(cfg, xh, yph, ph, nt, slabs=None):
+    from oracle import oracle as orc
+    xs, es, ps = cfg.xshape, cfg.embed_shape, cfg.prod_shape
+    x, yp, p = xh, yph, ph
+    if slabs is not None:   # a bounded sample: the leading `slabs` slabs of the outermost axis
+        xs = (slabs,) + tuple(xs[1:])
+        es = (slabs,) + tuple(es[1:])
+        ps = (slabs,) + tuple(ps[1:])
+        x = xh[:int(np.prod(xs))]
+        yp = yph[:int(np.prod(ps))]
+        p = ph[:int(np.prod(xs))]
+    t0 = time.perf_counter()
+    orc.embed(x, xs, es, "f64", nthreads=nt)
+    orc.product(x, xs, yp, ps, "f64", nthreads=nt)
+    orc.moment(p, xs, "f64", nthreads=nt)
+    dt = time.perf_counter() - t0
+    nI = int(np.prod([min(a, b) for a, b in zip(xs, ps)]))
+    nbytes = 8 * (int(np.prod(xs)) + int(np.prod(es))) + 24 * nI + 8 * int(np.prod(xs))
+    return nbytes, dt
+
+
+def cpu_baseline(args, cfg, xh, yph, ph):
+    nt = os.cpu_count() or 1
+    total_b, total_t, n = 0, 0.0, 0
+    while total_t < args.cpu_seconds or n == 0:
+        b, t = oracle_step(cfg, xh, yph, ph, nt, slabs=3)
+        total_b += b
+        total_t += t
+        n += 1
+    return {"value": round(total_b / total_t / 1e9, 3), "unit": "GB/s", "cores": nt, "kind": "oracle",
+            "sample": f"{n} oracle steps on the leading 3 of 9 outer slabs of the f64 d=8 workload "
+                      f"(embed+product+moment, outer-axis std::thread split), {total_t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, on this machine's host cores."""
+    if rank != 0:
+        return None
+    from paper_1608_00099_gb300 import synth
+    from oracle import build as ob
+    ob.build()
+    cfg = synth.config_f64_d8()
+    xh = cfg.x_values()
+    yph = cfg.yprod_values()
+    ph = synth.normalise(xh)
+    nt = os.cpu_count() or 1
+    slabs = 1   # one of the 9 outer slabs per step keeps K steps within minutes
+    for _ in range(args.warmup):
+        oracle_step(cfg, xh, yph, ph, nt, slabs=slabs)
+    tb, tt = 0, 0.0
+    for _ in range(args.steps):
+        b, t = oracle_step(cfg, xh, yph, ph, nt, slabs=slabs)
+        tb += b
+        tt += t
+    value = tb / tt / 1e9
+    sample = f"leading {slabs} of 9 outer slabs of the f64 d=8 workload per step (embed+product+moment)"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (SplitMix64 seed 1002, U(0,1))",
+            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": nt, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed load for the clock sampler")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--batch-reps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local, dist = dist_setup()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local, dist)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
