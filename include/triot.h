@@ -123,6 +123,28 @@ int triot_moment_workspace_size(int rank, const int64_t* shape, int dtype, size_
 int triot_moment(int rank, const int64_t* shape, const void* p, int dtype, double* out,
                  void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * triot_moment_noalloc -- the same result as triot_moment, for callers that cannot
+ *   allocate device memory and so cannot provide a workspace (for example code that runs
+ *   where cudaMalloc is forbidden or would synchronise the device, or an application
+ *   whose device memory is owned entirely by its own pool).  The paper has no
+ *   counterpart: this is a deployment convenience of this library.
+ *   The per-block partial sums go to a fixed scratch array of
+ *   TRIOT_MOMENT_NOALLOC_MAX_DOUBLES doubles (512 KiB) that lives in the library image;
+ *   every GPU that loads the library holds it until the process exits.  The call itself
+ *   allocates nothing (no cudaMalloc, no library allocator).
+ *   Arguments as triot_moment without the workspace.  Fails with TRIOT_ERR_WORKSPACE,
+ *   and enqueues nothing, when the launch would need more partials than the scratch
+ *   holds (rare: the partials number grid * (effective rank + 1), grid about SMs * 4).
+ *   The first call on a device looks up the scratch's device address (once, with that
+ *   device current); make that first call before any stream capture.  All calls share the
+ *   one scratch array, which keeps the last call's contents: calls whose kernels may
+ *   overlap on the GPU (different streams without ordering) race on it.
+ */
+#define TRIOT_MOMENT_NOALLOC_MAX_DOUBLES 65536
+int triot_moment_noalloc(int rank, const int64_t* shape, const void* p, int dtype, double* out,
+                         void* stream);
+
 /* ------------------------------------------------------------------ batched launch */
 
 /*

@@ -66,6 +66,7 @@ def lib() -> C.CDLL:
             "triot_product": (i, [i, _I64P, vp, _I64P, vp, i, vp]),
             "triot_moment_workspace_size": (i, [i, _I64P, i, C.POINTER(sz)]),
             "triot_moment": (i, [i, _I64P, vp, i, vp, vp, sz, vp]),
+            "triot_moment_noalloc": (i, [i, _I64P, vp, i, vp, vp]),
             "triot_batch_plan_create": (i, [C.POINTER(BatchDesc), i, i, i, C.POINTER(Tune), C.POINTER(vp)]),
             "triot_batch_run": (i, [vp, vp]),
             "triot_batch_run_plain": (i, [vp, vp]),
