@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 NOMINAL_HBM_GBS = 8000.0
+TUNE_FILE = os.path.join(ROOT, "paper_1608_00099_gb300", "tune_gb300.json")
 WORKLOAD = "f64_d8"
 WORKLOAD_DESC = ("f64 d=8: embed x 9^8 U(0,1) -> (11,10)x4; product y*=x over (9,8)x4 into U(0,1) "
                  "(12,8)x4; moment of x/sum(x)")
@@ -151,9 +152,15 @@ def run_ours(args, rank, world, local, dist):
     y2 = torch.from_numpy(yph.reshape(cfg.prod_shape)).to(dev)
     p = torch.from_numpy(ph.reshape(cfg.xshape)).to(dev)
     out = torch.empty(len(cfg.xshape) + 1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    tuning = None
+    if os.path.exists(TUNE_FILE) and not args.no_tune_file:
+        triot.triot_tune_load(TUNE_FILE)
+        tuning = {"loaded": os.path.relpath(TUNE_FILE, ROOT)}
+    if args.autotune:
+        tuning = {"autotuned": run_autotune(triot, cfg, x, y1, y2, p, dev, stream, args.autotune)}
     ws = torch.empty(triot.triot_moment_workspace_size(cfg.xshape, torch.float64) // 8 + 2,
                      dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream()
     b = step_bytes(cfg)
     step_total = sum(b.values())
 
@@ -230,8 +237,11 @@ def run_ours(args, rank, world, local, dist):
         "ops": ops, "roofline": roofline, "e2e": e2e, "gpu_launches": 4 * K,
         "clocks": clocks,
     }
+    result["tuning"] = tuning
     if not args.no_batch:
         result["batch"] = run_batch(args, triot, synth, dev, stream)
+    if not args.no_extra:
+        result["workloads"] = run_extra_workloads(args, triot, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args, cfg, xh, yph, ph)
     return result
@@ -346,6 +356,126 @@ def run_batch(args, triot, synth, dev, stream):
     return res
 
 
+def time_op(fn, reps, stream):
+    """Device time per call: the calls are captured once into a CUDA graph and the graph is
+    replayed, so host launch overhead (ctypes, planning) is not in the measurement."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for k in range(2):
+            fn(k, side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        for k in range(reps):
+            fn(k, side)
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 3
+    a.record(stream)
+    for _ in range(n):
+        g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / (n * reps)
+
+
+def op_entry(nbytes, ms, peak, elems=None):
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    d = {"us": round(ms * 1e3, 2), "bytes": int(nbytes), "gbs": round(gbs, 1),
+         "frac_8tbs": round(gbs / NOMINAL_HBM_GBS, 4), "frac_measured": round(gbs / peak, 4)}
+    if elems is not None:
+        d["elem_per_s"] = round(elems / (ms * 1e-3), 1)
+    return d
+
+
+def run_extra_workloads(args, triot, synth, dev, stream):
+    """Per-op figures on the other workloads (working sets under 4x L2 rotate copies)."""
+    import torch
+    peak, _ = measured_peak()
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    res = {}
+    # embed f64 d=6: 10 MB per call, rotated over enough copies to exceed 4x L2
+    cfg = synth.config_embed_small()
+    xh = cfg.x_values()
+    per = 8 * (int(np.prod(cfg.xshape)) + int(np.prod(cfg.embed_shape)))
+    ncopy = int(4 * l2 // per) + 1
+    xs = [torch.from_numpy(xh.reshape(cfg.xshape)).to(dev) for _ in range(ncopy)]
+    ys = [torch.empty(cfg.embed_shape, dtype=torch.float64, device=dev) for _ in range(ncopy)]
+    ms = time_op(lambda k, st: triot.triot_embed(xs[k % ncopy], ys[k % ncopy], stream=st), 4 * ncopy, stream)
+    res["embed_f64_d6"] = {"embed": op_entry(per, ms, peak, int(np.prod(cfg.embed_shape))), "copies_rotated": ncopy}
+    x2 = [torch.empty_like(xs[0]) for _ in range(ncopy)]
+    ms = time_op(lambda k, st: triot.triot_crop(x2[k % ncopy], ys[k % ncopy], stream=st), 4 * ncopy, stream)
+    res["embed_f64_d6"]["crop"] = op_entry(2 * 8 * int(np.prod(cfg.xshape)), ms, peak)
+    del xs, ys, x2
+    # f32 d=24: 44 GB embed target, product over the all-2 intersection, moment of x
+    cfg = synth.config_f32_d24()
+    ny = int(np.prod(cfg.embed_shape))
+    free, _ = torch.cuda.mem_get_info(dev)
+    xh = cfg.x_values().astype(np.float32)
+    x = torch.from_numpy(xh.reshape(cfg.xshape)).to(dev)
+    nx = xh.size
+    r = {}
+    if not args.no_big and free > 4 * ny + (8 << 30):
+        y = torch.empty(ny, dtype=torch.float32, device=dev).view(cfg.embed_shape)
+        ms = time_op(lambda k, st: triot.triot_embed(x, y, stream=st), 5, stream)
+        r["embed"] = op_entry(4 * (nx + ny), ms, peak, ny)
+        ms = time_op(lambda k, st: triot.triot_product(x, y, stream=st), 20, stream)
+        r["product"] = op_entry(3 * 4 * nx, ms, peak, nx)
+        del y
+        torch.cuda.empty_cache()
+    if True:
+        out = torch.empty(25, dtype=torch.float64, device=dev)
+        ws = torch.empty(triot.triot_moment_workspace_size(cfg.xshape, torch.float32) // 8 + 2,
+                         dtype=torch.float64, device=dev)
+        ms = time_op(lambda k, st: triot.triot_moment(x, out=out, workspace=ws, stream=st), 20, stream)
+        r["moment"] = op_entry(4 * nx, ms, peak, nx)
+        res["f32_d24"] = r
+        del x
+        torch.cuda.empty_cache()
+    # precision workload: crop p to the intersection, r *= q, moment of r; bf16 / f16 / f64
+    pc = synth.config_precision()
+    I = tuple(min(a, b) for a, b in zip(pc.pshape, pc.qshape))
+    nI = int(np.prod(I))
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f64": torch.float64}
+    for name, dt in tdt.items():
+        es = 8 if name == "f64" else 2
+        pt = synth.to_storage(pc.p64, name).reshape(pc.pshape)
+        qt = synth.to_storage(pc.q64, name).reshape(pc.qshape)
+        per = es * (pt.numel() + qt.numel() + nI)
+        ncopy = int(4 * l2 // per) + 1
+        P = [pt.to(dev) for _ in range(ncopy)]
+        Q = [qt.to(dev) for _ in range(ncopy)]
+        R = [torch.empty(I, dtype=dt, device=dev) for _ in range(ncopy)]
+        out = torch.empty(len(I) + 1, dtype=torch.float64, device=dev)
+        ws = torch.empty(triot.triot_moment_workspace_size(I, dt) // 8 + 2, dtype=torch.float64, device=dev)
+        r = {"copies_rotated": ncopy, "intersection": list(I)}
+        ms = time_op(lambda k, st: triot.triot_crop(R[k % ncopy], P[k % ncopy], stream=st), 3 * ncopy, stream)
+        r["crop"] = op_entry(2 * es * nI, ms, peak, nI)
+        ms = time_op(lambda k, st: triot.triot_product(Q[k % ncopy], R[k % ncopy], stream=st), 3 * ncopy, stream)
+        r["product"] = op_entry(3 * es * nI, ms, peak, nI)
+        ms = time_op(lambda k, st: triot.triot_moment(R[k % ncopy], out=out, workspace=ws, stream=st), 3 * ncopy, stream)
+        r["moment"] = op_entry(es * nI, ms, peak, nI)
+        res[f"precision_{name}"] = r
+        del P, Q, R
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_autotune(triot, cfg, x, y1, y2, p, dev, stream, path):
+    import torch
+    ws = torch.empty(triot.MOMENT_MAX_WORKSPACE_PER_RANK * (len(cfg.xshape) + 1) // 8, dtype=torch.float64,
+                     device=dev)
+    t = {"embed": triot.triot_autotune(triot.OP_EMBED, x, y1, stream=stream),
+         "product": triot.triot_autotune(triot.OP_PRODUCT, x, y2, stream=stream),
+         "moment": triot.triot_autotune(triot.OP_MOMENT, p, None, workspace=ws, stream=stream)}
+    if path:
+        triot.triot_tune_save(path)
+    return t
+
+
 # ------------------------------------------------------------------ the oracle on the host
 
 def oracle_step(cfg, xh, yph, ph, nt, slabs=None):
@@ -426,6 +556,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads' per-op figures")
+    ap.add_argument("--no-big", action="store_true", help="skip the 44 GB f32 d=24 workload")
+    ap.add_argument("--autotune", default="", help="autotune the three ops and save the cache here")
+    ap.add_argument("--no-tune-file", action="store_true", help="ignore the committed tuning file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

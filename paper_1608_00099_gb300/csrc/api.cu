@@ -108,18 +108,17 @@ int launch_rows(int op, int rank, const int64_t* xshape, const void* x, const in
 }
 
 // ------------------------------------------------------------------ moment
-static int moment_occupancy(int dtype, int D, int& occ) {
+static int moment_occupancy(const void* fn, int threads, int& occ) {
   static std::mutex mu;
-  static int table[4][kMaxRank + 1] = {};
+  static std::vector<std::pair<const void*, int>> table;
   std::lock_guard<std::mutex> lk(mu);
-  if (!table[dtype][D]) {
-    const void* fn = moment_kernel_ptr(dtype, D);
-    int o = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kMomentWarps * 32, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    table[dtype][D] = o > 0 ? o : 1;
-  }
-  occ = table[dtype][D];
+  for (const auto& kv : table)
+    if (kv.first == fn) { occ = kv.second; return TRIOT_OK; }
+  int o = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  occ = o > 0 ? o : 1;
+  table.emplace_back(fn, occ);
   return TRIOT_OK;
 }
 
@@ -132,10 +131,13 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
   if (st) return fail(st, err);
   DeviceInfo dev;
   if ((st = device_info(dev))) return st;
+  const int m = moment_block_axes(c, dtype);
+  const void* fn = moment_kernel_ptr(dtype, c.D, m);
+  if (!fn) return fail(TRIOT_ERR_RANK, "no moment kernel for this effective rank");
   int occ = 1;
-  if ((st = moment_occupancy(dtype, c.D, occ))) return st;
+  if ((st = moment_occupancy(fn, (m > 0 ? kMomentBlkWarps : kMomentWarps) * 32, occ))) return st;
   TuneCfg t = force ? *force : tune_lookup(TRIOT_OP_MOMENT, dtype, c);
-  plan_moment(c, rank, dtype_size(dtype), p, t, dev, occ, L);
+  plan_moment(c, rank, dtype_size(dtype), m, p, t, dev, occ, L);
   if (L.grid > kMaxMomentParts) return fail(TRIOT_ERR_ARG, "moment grid exceeds the partial limit");
   return TRIOT_OK;
 }
@@ -149,11 +151,11 @@ int launch_moment(const MomentLaunch& L, int dtype, const void* p, double* out, 
                   cudaStream_t stream) {
   cudaError_t e;
   if (!L.empty) {
-    const void* fn = moment_kernel_ptr(dtype, L.g.D);
+    const void* fn = moment_kernel_ptr(dtype, L.g.D, L.g.m);
     if (!fn) return fail(TRIOT_ERR_RANK, "no moment kernel for this effective rank");
     double* part = static_cast<double*>(ws);
     void* args[] = {(void*)&L.g, (void*)&p, (void*)&part};
-    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(kMomentWarps * 32), args, 0, stream);
+    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.warps * 32), args, 0, stream);
     if (e != cudaSuccess) return cuda_fail(e, "moment kernel launch");
   }
   const double* partc = static_cast<const double*>(ws);

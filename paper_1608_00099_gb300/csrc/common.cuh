@@ -8,7 +8,8 @@
 namespace triot {
 
 constexpr int kMaxRank = 24;
-constexpr int kMomentWarps = 4;  // warps per CTA of the moment kernels
+constexpr int kMomentWarps = 4;  // warps per CTA of the row-mode moment kernels
+constexpr int kMomentBlkWarps = 2;  // warps per CTA of the block-column moment kernel
 
 enum RowOp { ROW_EMBED = 0, ROW_CROP = 1, ROW_PRODUCT = 2 };
 
@@ -75,7 +76,9 @@ enum {
 // ------------------------------------------------------------------ moment
 struct MomentGeom {
   int D;                           // effective rank
-  int nchunks;                     // chunks per lane segment
+  int m;                           // block mode: the last m axes form blocks of B elements
+  int B;                           // (m = 0: row mode, the inner axis alone)
+  int nchunks;                     // chunks per lane segment (the last may be partial)
   long long n;                     // elements
   long long seg;                   // lane segment length S (multiple of the chunk)
   long long nwarpseg;              // warp segments (32 lane segments each)

@@ -8,7 +8,9 @@ namespace triot {
 const void* embed_kernel_ptr(int es, int nouter);
 const void* crop_kernel_ptr(int es, int nouter);
 const void* product_kernel_ptr(int dtype, int nouter);
-// moment kernels by dtype and effective rank D in [1, 24]
-const void* moment_kernel_ptr(int dtype, int D);
+// moment kernels by dtype and effective rank D in [1, 24]; m > 0 selects the block-column
+// kernel (f32/bf16/f16 only) with D - m outer axes
+const void* moment_kernel_ptr(int dtype, int D, int m = 0);
+const void* moment_blk_kernel_ptr(int dtype, int DO);
 const void* combine_kernel_ptr();
 }  // namespace triot

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(kMomentWarps * 32) moment_f32_kernel(
   for (int i = 0; i < D; ++i) t[i] = 0;
   float mp = 0.f, wp = 0.f, jl = 0.f;  // segment mass, local-index-weighted mass, local index
   uint32_t t0 = 0;                      // inner index at the start of the current run
+  bool active = false;                  // the current lane segment starts inside the tensor
 
   // end of a run of one row: push the run into the row accumulators
   auto flush_run = [&]() {
@@ -204,26 +205,33 @@ __global__ void __launch_bounds__(kMomentWarps * 32) moment_f32_kernel(
     cp_async_wait1();
     __syncwarp();
     if (chunk == 0) {
-      decode_tuple<D>(g, (ws * 32 + lane) * g.seg, t);
-      t0 = t[D - 1];
-    }
-    const unsigned char* row = stage[warp][s & 1] + lane * kStageRowBytes;
-#pragma unroll 4
-    for (int j = 0; j < C; ++j) {
-      const float x = elem_f32<T>(row, j);
-      mp += x;
-      wp = fmaf(jl, x, wp);
-      jl += 1.0f;
-      if (++t[D - 1] == L) {
-        flush_run();
-        t[D - 1] = 0;
-        t0 = 0;
-        carry();
+      // a lane segment that starts at or past the end holds only zero fill: skip it
+      const long long k0 = (ws * 32 + lane) * g.seg;
+      active = k0 < g.n;
+      if (active) {
+        decode_tuple<D>(g, k0, t);
+        t0 = t[D - 1];
       }
     }
-    flush_run();
-    t0 = t[D - 1];
-    if (chunk == g.nchunks - 1) flush_all();
+    if (active) {
+      const unsigned char* row = stage[warp][s & 1] + lane * kStageRowBytes;
+#pragma unroll 4
+      for (int j = 0; j < C; ++j) {
+        const float x = elem_f32<T>(row, j);
+        mp += x;
+        wp = fmaf(jl, x, wp);
+        jl += 1.0f;
+        if (++t[D - 1] == L) {
+          flush_run();
+          t[D - 1] = 0;
+          t0 = 0;
+          carry();
+        }
+      }
+      flush_run();
+      t0 = t[D - 1];
+      if (chunk == g.nchunks - 1) flush_all();
+    }
     __syncwarp();
   }
 
@@ -250,88 +258,91 @@ __global__ void __launch_bounds__(kMomentWarps * 32) moment_f32_kernel(
   }
 }
 
-// ====================================================================== f64 fixed point
+// ====================================================================== f32, short rows
 //
-// A chunk's elements are converted to integers relative to the chunk's largest exponent
-// E_c: an f64 with biased exponent e and significand m (53 bits, implicit bit included)
-// is m * 2^(e-1075); relative to E_c it is (m >> (E_c - e)) units of 2^(E_c-1075)
-// (truncation below the chunk maximum's last bit).  Runs are summed in 64-bit integers,
-// then moved to the lane's 128-bit accumulators, whose unit is 2^(E_L - 1075 - 16) for
-// the largest exponent E_L the lane has seen (accumulators are shifted right when E_L
-// grows).  Non-finite elements are summed separately in f64 so that they propagate.
+// Block-column mode, for inner extents of at most kBlkMax elements.  The last m axes form
+// a block of B <= kBlkMax elements and lane segments are whole numbers of blocks.  An
+// element at position j of its block adds its value to the lane's column sum cs[j] (shared
+// memory) and to the block's mass; at a block end the block's mass is carried up the
+// DO = D - m outer axes exactly as a row's mass is in row mode.  The inner axes need no
+// per-element work at all: at the end, m_a = sum_j digit_a(j) * colsum[j] for each of the m
+// block axes.  Column sums are folded into compensated f32 pairs at each segment end, so
+// no plain f32 sum runs over more than one segment.
+constexpr int kBlkMax = 16;
+constexpr int kColStride = kBlkMax + 1;  // odd stride: lanes at the same column hit distinct banks
+constexpr int kBlkWarps = kMomentBlkWarps;  // warps per CTA (keeps static shared memory < 48 KB)
 
-template <int D>
-__global__ void __launch_bounds__(kMomentWarps * 32) moment_f64_kernel(
-    const __grid_constant__ MomentGeom g, const double* __restrict__ p,
-    double* __restrict__ partial) {
-  constexpr int ES = 8;
-  constexpr int C = 16;
-  __shared__ __align__(16) unsigned char stage[kMomentWarps][2][kStageBytes];
-  __shared__ double wsum[kMomentWarps][kMaxRank + 1];
+template <typename T, int DO>
+__global__ void __launch_bounds__(kBlkWarps * 32) moment_blk_kernel(
+    const __grid_constant__ MomentGeom g, const T* __restrict__ p, double* __restrict__ partial) {
+  constexpr int ES = sizeof(T);
+  constexpr int C = 128 / ES;
+  constexpr int NO = DO > 0 ? DO : 1;
+  __shared__ __align__(16) unsigned char stage[kBlkWarps][2][kStageBytes];
+  __shared__ float s_cs[kBlkWarps][32][kColStride];       // current segment
+  __shared__ float s_ch[kBlkWarps][32][kColStride];       // folded: value
+  __shared__ float s_ce[kBlkWarps][32][kColStride];       // folded: compensation
+  __shared__ double wsum[kBlkWarps][kMaxRank + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * kMomentWarps + warp;
-  const long long tw = (long long)gridDim.x * kMomentWarps;
+  const long long gw = (long long)blockIdx.x * kBlkWarps + warp;
+  const long long tw = (long long)gridDim.x * kBlkWarps;
   const long long nseg = gw < g.nwarpseg ? (g.nwarpseg - gw + tw - 1) / tw : 0;
   const long long nsteps = nseg * g.nchunks;
   const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
-  const uint32_t L = (uint32_t)g.ext[D - 1];
+  const int B = g.B, m = g.m;
+  float* cs = s_cs[warp][lane];
+  float* ch = s_ch[warp][lane];
+  float* ce = s_ce[warp][lane];
+  for (int j = 0; j < B; ++j) { cs[j] = 0.f; ch[j] = 0.f; ce[j] = 0.f; }
 
-  __int128 A[D], P[D];
+  Comp32 A[NO], P[NO + 1];  // A[i]: outer axis i; P[0]: mass; P[k]: pending of level k-1
 #pragma unroll
-  for (int i = 0; i < D; ++i) { A[i] = 0; P[i] = 0; }
-  int EL = 0;                         // lane reference exponent (0: nothing seen yet)
-  bool special = false;               // a non-finite element was seen
-  double Asp[D], Psp = 0.0;           // f64 sums of non-finite elements
+  for (int i = 0; i < NO; ++i) A[i].zero();
 #pragma unroll
-  for (int i = 0; i < D; ++i) Asp[i] = 0.0;
-  uint32_t t[D];
+  for (int i = 0; i <= NO; ++i) P[i].zero();
+  uint32_t t[NO];
 #pragma unroll
-  for (int i = 0; i < D; ++i) t[i] = 0;
-  long long mp = 0, wp = 0;           // run sums in units of 2^(Ec-1075)
-  long long jl = 0;                   // local index within the run
-  uint32_t t0 = 0;
-  int Ec = 1;
+  for (int i = 0; i < NO; ++i) t[i] = 0;
+  float bm = 0.f;  // mass of the current block
+  int jb = 0;      // position in the current block
+  bool active = false;
 
-  auto flush_run = [&]() {
-    if (mp != 0 || wp != 0) {
-      if (Ec > EL) {
-        if (EL != 0) {
+  auto block_end = [&]() {
+    if (DO == 0) {
+      P[0].add(bm);
+    } else {
+      P[DO].s = bm;
+      P[DO].e = 0.f;
 #pragma unroll
-          for (int i = 0; i < D; ++i) { A[i] = shr_arith(A[i], Ec - EL); P[i] = shr_arith(P[i], Ec - EL); }
+      for (int i = DO - 1; i >= 0; --i) {
+        const float pm = P[i + 1].value();
+        A[i].add((float)t[i] * pm);
+        P[i].add(pm);
+        P[i + 1].zero();
+        if (i > 0) {
+          if (++t[i] < (uint32_t)g.ext[i]) break;
+          t[i] = 0;
+        } else {
+          ++t[0];
         }
-        EL = Ec;
-      }
-      const int sc = kFixGuard - (EL - Ec);
-      const __int128 M = (__int128)mp;
-      const __int128 W = (__int128)wp + (__int128)t0 * (__int128)mp;
-      P[D - 1] += scale_shift(M, sc);
-      A[D - 1] += scale_shift(W, sc);
-    }
-    mp = 0; wp = 0; jl = 0;
-  };
-  auto carry = [&]() {
-#pragma unroll
-    for (int i = D - 2; i >= 0; --i) {
-      const __int128 pm = P[i + 1];
-      A[i] += pm * (__int128)t[i];
-      P[i] += pm;
-      P[i + 1] = 0;
-      if (i > 0) {
-        if (++t[i] < (uint32_t)g.ext[i]) break;
-        t[i] = 0;
-      } else {
-        ++t[0];
       }
     }
+    bm = 0.f;
   };
-  auto flush_all = [&]() {
-    flush_run();
+  auto flush_levels = [&]() {
 #pragma unroll
-    for (int i = D - 2; i >= 0; --i) {
-      const __int128 pm = P[i + 1];
-      A[i] += pm * (__int128)t[i];
-      P[i] += pm;
-      P[i + 1] = 0;
+    for (int i = DO - 2; i >= 0; --i) {
+      const float pm = P[i + 1].value();
+      A[i].add((float)t[i] * pm);
+      P[i].add(pm);
+      P[i + 1].zero();
+    }
+    for (int j = 0; j < B; ++j) {  // fold this segment's column sums
+      const float v = cs[j], s0 = ch[j];
+      const float tt = s0 + v, bp = tt - s0;
+      ce[j] += (s0 - (tt - bp)) + (v - bp);
+      ch[j] = tt;
+      cs[j] = 0.f;
     }
   };
 
@@ -350,52 +361,275 @@ __global__ void __launch_bounds__(kMomentWarps * 32) moment_f64_kernel(
     cp_async_wait1();
     __syncwarp();
     if (chunk == 0) {
-      decode_tuple<D>(g, (ws * 32 + lane) * g.seg, t);
-      t0 = t[D - 1];
-    }
-    const unsigned long long* row =
-        reinterpret_cast<const unsigned long long*>(stage[warp][s & 1] + lane * kStageRowBytes);
-    // the chunk's largest finite exponent (zeros and subnormals count as 1)
-    int emax = 1;
-    bool chunk_special = false;
+      const long long k0 = (ws * 32 + lane) * g.seg;
+      active = k0 < g.n;
+      if (active && DO > 0) {
+        // outer digits of the segment's first block (segments start on block boundaries)
+        long long rem = k0 / B;
+        if (g.n32) {
+          uint32_t r32 = (uint32_t)rem;
 #pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const int e = (int)((row[j] >> 52) & 0x7FF);
-      chunk_special |= (e == 0x7FF);
-      emax = (e != 0x7FF && e > emax) ? e : emax;
-    }
-    // a run never spans two chunks, so it has one exponent
-    Ec = emax;
-    special |= chunk_special;
-#pragma unroll 4
-    for (int j = 0; j < C; ++j) {
-      const unsigned long long bits = row[j];
-      const int e = (int)((bits >> 52) & 0x7FF);
-      if (chunk_special && e == 0x7FF) {
-        const double v = __longlong_as_double((long long)bits);
+          for (int i = DO - 1; i >= 1; --i) {
+            const uint32_t q = fdiv(r32, g.div[i]);
+            t[i] = r32 - q * g.div[i].d;
+            r32 = q;
+          }
+          t[0] = r32;
+        } else {
 #pragma unroll
-        for (int i = 0; i < D; ++i) Asp[i] += v * (double)t[i];
-        Psp += v;
-      } else {
-        const unsigned long long m =
-            (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-        const int sh = Ec - (e ? e : 1);
-        long long c = sh < 64 ? (long long)(m >> sh) : 0ll;
-        c = (bits >> 63) ? -c : c;
-        mp += c;
-        wp += jl * c;
+          for (int i = DO - 1; i >= 1; --i) {
+            const long long q = rem / g.ext[i];
+            t[i] = (uint32_t)(rem - q * g.ext[i]);
+            rem = q;
+          }
+          t[0] = (uint32_t)rem;
+        }
       }
-      ++jl;
-      if (++t[D - 1] == L) {
-        flush_run();
-        t[D - 1] = 0;
-        t0 = 0;
+      jb = 0;
+    }
+    if (active) {
+      const unsigned char* row = stage[warp][s & 1] + lane * kStageRowBytes;
+      const long long left = g.seg - (long long)chunk * C;
+      const int cnt = left < C ? (int)left : C;
+#pragma unroll 4
+      for (int j = 0; j < cnt; ++j) {
+        const float x = elem_f32<T>(row, j);
+        cs[jb] += x;
+        bm += x;
+        if (++jb == B) {
+          jb = 0;
+          block_end();
+        }
+      }
+      if (chunk == g.nchunks - 1) flush_levels();
+    }
+    __syncwarp();
+  }
+
+  // column sums of the warp: lane j < B adds column j over the 32 lanes (compensated),
+  // then turns it into its contribution to each block axis: digit_a(j) * colsum_j
+  Comp32 Ain[kMaxRank];
+#pragma unroll
+  for (int a = 0; a < kMaxRank; ++a) Ain[a].zero();
+  __syncwarp();
+  if (lane < B) {
+    Comp32 col;
+    col.zero();
+    for (int l = 0; l < 32; ++l) {
+      col.add(s_ch[warp][l][lane]);
+      col.e += s_ce[warp][l][lane];
+    }
+    const float cv = col.value();
+    uint32_t u = (uint32_t)lane;
+    for (int a = DO + m - 1; a >= DO; --a) {  // block axes, innermost digit first
+      const uint32_t e = (uint32_t)g.ext[a];
+      const uint32_t d = u % e;
+      u /= e;
+      Ain[a - DO].add((float)d * cv);
+    }
+  }
+
+  // warp reduction of the compensated pairs (xor butterfly: fixed order); the register
+  // arrays are indexed with compile-time indices only
+  double* ws_out = wsum[warp];
+  const int D = DO + m;
+  auto reduce_out = [&](Comp32 v, int slot) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, v.s, off);
+      const float oe = __shfl_xor_sync(0xffffffffu, v.e, off);
+      v.add(os);
+      v.e += oe;
+    }
+    if (lane == 0) ws_out[slot] = (double)v.s + (double)v.e;
+  };
+#pragma unroll
+  for (int i = 0; i < DO; ++i) reduce_out(A[i], i);
+  for (int a = 0; a < m; ++a) reduce_out(Ain[a], DO + a);
+  reduce_out(P[0], D);
+  __syncthreads();
+  if (threadIdx.x <= D) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBlkWarps; ++w) acc += wsum[w][threadIdx.x];
+    partial[(long long)blockIdx.x * (D + 1) + threadIdx.x] = acc;
+  }
+}
+
+// ====================================================================== f64 fixed point
+//
+// Each lane reads its 16-element chunk from shared memory twice.  First pass: the chunk's
+// largest exponent field E_c (zeros and subnormals count as exponent 1) and whether a
+// non-finite value is present.  Second pass, one run at a time (a run = the part of the
+// chunk inside one row): an f64 with biased exponent e and significand m (53 bits,
+// implicit bit included) is m * 2^(e-1075); relative to E_c it is c = m >> (E_c - e)
+// units of 2^(E_c-1075), exact for the chunk maximum and truncated below its last bit
+// for smaller elements.  A run keeps P = sum c and Q = sum of the running P, so that the
+// run's inner-index-weighted sum sum_k k c_k = n P - Q needs no multiply per element.
+// Runs move into the lane's 128-bit accumulators, whose unit is 2^(E_L-1075-16) for the
+// largest exponent E_L the lane has seen (accumulators shift right when E_L grows).
+// Non-finite elements are summed separately in f64 so that they propagate.
+
+template <int D>
+__global__ void __launch_bounds__(kMomentWarps * 32, (D <= 12 ? 4 : 2)) moment_f64_kernel(
+    const __grid_constant__ MomentGeom g, const double* __restrict__ p,
+    double* __restrict__ partial) {
+  constexpr int ES = 8;
+  constexpr int C = 16;
+  __shared__ __align__(16) unsigned char stage[kMomentWarps][2][kStageBytes];
+  __shared__ double wsum[kMomentWarps][kMaxRank + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kMomentWarps + warp;
+  const long long tw = (long long)gridDim.x * kMomentWarps;
+  const long long nseg = gw < g.nwarpseg ? (g.nwarpseg - gw + tw - 1) / tw : 0;
+  const long long nsteps = nseg * g.nchunks;
+  const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
+  const uint32_t L = (uint32_t)g.ext[D - 1];
+
+  __int128 A[D], P[D];  // P[0]: mass; P[k], k >= 1: pending mass of the block of axis k-1
+#pragma unroll
+  for (int i = 0; i < D; ++i) { A[i] = 0; P[i] = 0; }
+  int EL = 0;                         // lane reference exponent (0: nothing seen yet)
+  bool special = false;               // a non-finite element was seen
+  double Asp[D], Psp = 0.0;           // f64 sums of non-finite elements
+#pragma unroll
+  for (int i = 0; i < D; ++i) Asp[i] = 0.0;
+  uint32_t t[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) t[i] = 0;
+  uint32_t ti = 0;                    // inner index (digit of axis D-1)
+  bool active = false;                // the current lane segment starts inside the tensor
+
+  // a run (P: sum of c, W: sum of local index * c, t0: inner index of its first element)
+  auto add_run = [&](long long Pr, long long Wr, uint32_t t0, int Ec) {
+    if (Pr == 0 && Wr == 0) return;
+    if (Ec > EL) {
+      if (EL != 0) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) { A[i] = shr_arith(A[i], Ec - EL); P[i] = shr_arith(P[i], Ec - EL); }
+      }
+      EL = Ec;
+    }
+    const __int128 M = (__int128)Pr;
+    const __int128 W = (__int128)Wr + (__int128)Pr * (__int128)(unsigned long long)t0;
+    if (EL == Ec) {
+      P[D - 1] += M << kFixGuard;
+      A[D - 1] += W << kFixGuard;
+    } else {
+      const int sc = kFixGuard - (EL - Ec);
+      P[D - 1] += scale_shift(M, sc);
+      A[D - 1] += scale_shift(W, sc);
+    }
+  };
+  // row end: the row's pending mass moves up while axes wrap (carry of Algorithm 3)
+  auto carry = [&]() {
+#pragma unroll
+    for (int i = D - 2; i >= 0; --i) {
+      const __int128 pm = P[i + 1];
+      A[i] += pm * (__int128)(unsigned long long)t[i];
+      P[i] += pm;
+      P[i + 1] = 0;
+      if (i > 0) {
+        if (++t[i] < (uint32_t)g.ext[i]) break;
+        t[i] = 0;
+      } else {
+        ++t[0];
+      }
+    }
+  };
+  auto flush_levels = [&]() {
+#pragma unroll
+    for (int i = D - 2; i >= 0; --i) {
+      const __int128 pm = P[i + 1];
+      A[i] += pm * (__int128)(unsigned long long)t[i];
+      P[i] += pm;
+      P[i + 1] = 0;
+    }
+  };
+  // one chunk, runs split at row ends; SPECIAL chunks route non-finite values to f64
+  auto do_chunk = [&](const unsigned long long* row, int Ec, auto special_tag) {
+    constexpr bool SPECIAL = decltype(special_tag)::value;
+    int j = 0;
+    while (j < C) {
+      // active lanes keep ti < L, so every run has at least one element
+      const int left = ti < L ? (int)(L - ti) : C;
+      const int n = left < C - j ? left : C - j;
+      long long Pr = 0, Q = 0;
+      for (int k = 0; k < n; ++k) {
+        const unsigned long long b = row[j + k];
+        const uint32_t hi = (uint32_t)(b >> 32);
+        const uint32_t ef = hi & 0x7FF00000u;
+        if (SPECIAL && ef == 0x7FF00000u) {
+          const double v = __longlong_as_double((long long)b);
+#pragma unroll
+          for (int i = 0; i < D - 1; ++i) Asp[i] += v * (double)t[i];
+          Asp[D - 1] += v * (double)(ti + (uint32_t)k);
+          Psp += v;
+          Q += Pr;
+          continue;
+        }
+        const uint32_t e = (ef > 0x00100000u ? ef : 0x00100000u) >> 20;
+        const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
+        const uint32_t sh = (uint32_t)Ec - e;
+        long long c = (long long)(m >> (sh < 63u ? sh : 63u));
+        c = ((int)hi < 0) ? -c : c;
+        Pr += c;
+        Q += Pr;
+      }
+      add_run(Pr, (long long)n * Pr - Q, ti, Ec);
+      j += n;
+      ti += (uint32_t)n;
+      if (ti == L) {
+        ti = 0;
         carry();
       }
     }
-    flush_run();
-    t0 = t[D - 1];
-    if (chunk == g.nchunks - 1) flush_all();
+  };
+
+  if (nsteps > 0) {
+    stage_chunk<ES>(g, pb, stage[warp][0], gw, 0, lane);
+    cp_async_commit();
+  }
+  for (long long s = 0; s < nsteps; ++s) {
+    const long long ws = gw + (s / g.nchunks) * tw;
+    const int chunk = (int)(s % g.nchunks);
+    if (s + 1 < nsteps) {
+      const long long ws1 = gw + ((s + 1) / g.nchunks) * tw;
+      stage_chunk<ES>(g, pb, stage[warp][(s + 1) & 1], ws1, (int)((s + 1) % g.nchunks), lane);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
+    if (chunk == 0) {
+      // a lane segment that starts at or past the end holds only zero fill: skip it (for
+      // D = 1 its decoded inner index would not be below L)
+      const long long k0 = (ws * 32 + lane) * g.seg;
+      active = k0 < g.n;
+      if (active) {
+        decode_tuple<D>(g, k0, t);
+        ti = t[D - 1];
+      }
+    }
+    if (active) {
+    const unsigned long long* row =
+        reinterpret_cast<const unsigned long long*>(stage[warp][s & 1] + lane * kStageRowBytes);
+    // largest exponent field of the chunk (zeros and subnormals count as exponent 1)
+    uint32_t emaxf = 0x00100000u, efin = 0x00100000u;
+#pragma unroll
+    for (int j = 0; j < C; j += 2) {
+      const uint4 v = *reinterpret_cast<const uint4*>(row + j);
+      const uint32_t f0 = v.y & 0x7FF00000u, f1 = v.w & 0x7FF00000u;
+      emaxf = max(emaxf, max(f0, f1));
+      efin = max(efin, max(f0 == 0x7FF00000u ? 0u : f0, f1 == 0x7FF00000u ? 0u : f1));
+    }
+    if (emaxf != 0x7FF00000u) {
+      do_chunk(row, (int)(emaxf >> 20), std::false_type());
+    } else {
+      special = true;
+      do_chunk(row, (int)(efin >> 20), std::true_type());
+    }
+    if (chunk == g.nchunks - 1) flush_levels();
+    }
     __syncwarp();
   }
 

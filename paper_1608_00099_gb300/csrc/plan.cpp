@@ -203,6 +203,11 @@ void plan_rows(int op, const Canon& c, bool x_empty, int es, const void* A, cons
   g.path = vec_ok ? PATH_VEC : (row_ok ? PATH_ROW : PATH_GEN);
 
   long long target = t.tile_elems > 0 ? t.tile_elems : (32768 / es);
+  // small problems: shrink tiles so that every SM gets several (down to 64 vectors)
+  if (t.tile_elems <= 0) {
+    const long long spread = (c.total + 4ll * dev.sms - 1) / (4ll * dev.sms);
+    target = std::min(target, std::max(64ll * vec, spread));
+  }
   if (target < vec) target = vec;
   if (g.inner <= target) {
     long long R = std::max(1ll, target / g.inner);
@@ -238,7 +243,8 @@ long long moment_segment(const Canon& c, int es, long long target_lanes) {
   // the inner extent L (and of L * s_{D-2}), every lane of a warp reaches its row ends
   // (and the next carries) at the same step, so the carry code runs without divergence.
   // Each segment costs a tuple decode and a flush of D levels (~24 D instructions), so
-  // segments are at least 24 D elements long.
+  // segments are preferably at least 24 D elements long -- unless the tensor is too small
+  // to give every lane of a full GPU some work, in which case parallelism wins.
   const long long C = 128 / es;
   const long long L = c.ext[c.D - 1];
   auto lcm = [](long long a, long long b) { return a / gcd_ll(a, b) * b; };
@@ -249,13 +255,28 @@ long long moment_segment(const Canon& c, int es, long long target_lanes) {
     if (blk > 0 && blk <= 4096 && lcm(C, blk) <= 4096) base1 = lcm(C, blk);
   }
   const long long smin = std::max(C, 24ll * c.D);
-  auto up = [&](long long b) { return (smin + b - 1) / b * b; };
-  const long long s1 = up(base1);
-  if (c.total >= s1 * target_lanes) return s1;
-  return up(base0);
+  auto up = [&](long long b, long long lo) { return (lo + b - 1) / b * b; };
+  const long long cands[4] = {up(base1, smin), up(base0, smin), base0, C};
+  for (long long s : cands)
+    if (c.total >= s * target_lanes) return s;
+  // too small for every lane: the largest chunk multiple that still fills the lanes
+  long long s = (c.total / std::max(1ll, target_lanes)) / C * C;
+  return std::max(C, s);
 }
 
-void plan_moment(const Canon& c, int rank, int es, const void* p, const TuneCfg& t,
+int moment_block_axes(const Canon& c, int dtype) {
+  if (dtype == DT_F64) return 0;
+  long long b = 1;
+  int m = 0;
+  for (int a = c.D - 1; a >= 0; --a) {
+    if (b * c.ext[a] > 16) break;
+    b *= c.ext[a];
+    ++m;
+  }
+  return m;
+}
+
+void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
                  const DeviceInfo& dev, int occ, MomentLaunch& L) {
   MomentGeom& g = L.g;
   g = MomentGeom();
@@ -270,12 +291,34 @@ void plan_moment(const Canon& c, int rank, int es, const void* p, const TuneCfg&
   g.aligned = (reinterpret_cast<uintptr_t>(p) % 16) == 0;
   const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
   const long long max_ctas = (long long)dev.sms * std::max(1, cps);
-  const long long target_lanes = max_ctas * kMomentWarps * 32;
+  const int warps = m > 0 ? kMomentBlkWarps : kMomentWarps;
+  L.warps = warps;
+  const long long target_lanes = max_ctas * warps * 32;
   const long long C = 128 / es;
-  g.seg = moment_segment(c, es, target_lanes);
-  g.nchunks = (int)(g.seg / C);
+  g.m = m;
+  if (m > 0) {
+    long long B = 1;
+    for (int a = D - m; a < D; ++a) B *= c.ext[a];
+    g.B = (int)B;
+    // segments: whole blocks, 16-byte aligned starts; long enough to amortise the decode
+    // and flush of the D - m outer levels and the B column folds, unless that starves lanes
+    const long long al = 16 / es;
+    const long long base = B / gcd_ll(B, al) * al;
+    const long long smin = 24ll * (D - m) + 8ll * B + C;
+    long long S = (smin + base - 1) / base * base;
+    if (c.total < S * target_lanes) {
+      const long long fill = (c.total / std::max(1ll, target_lanes)) / base * base;
+      S = std::max(base, std::min(S, fill));
+    }
+    g.seg = S;
+    g.nchunks = (int)((S + C - 1) / C);
+  } else {
+    g.B = 0;
+    g.seg = moment_segment(c, es, target_lanes);
+    g.nchunks = (int)(g.seg / C);
+  }
   g.nwarpseg = c.empty ? 0 : (c.total + 32 * g.seg - 1) / (32 * g.seg);
-  long long need = (g.nwarpseg + kMomentWarps - 1) / kMomentWarps;
+  long long need = (g.nwarpseg + warps - 1) / warps;
   long long grid = std::min(need, max_ctas);
   L.empty = c.empty;
   L.grid = c.empty ? 0 : (int)std::max(1ll, grid);

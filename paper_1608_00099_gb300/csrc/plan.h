@@ -42,11 +42,15 @@ struct MomentLaunch {
   MomentGeom g;
   CombineGeom cg;
   int grid = 0;        // CTAs of the moment kernel (= number of partial vectors)
+  int warps = 4;       // warps per CTA
   bool empty = false;  // nothing to sum: only the combine runs (it writes zeros)
 };
 // `occ` = resident CTAs per SM of the chosen kernel (from the occupancy calculator).
-void plan_moment(const Canon& c, int rank, int es, const void* p, const TuneCfg& t,
+void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
                  const DeviceInfo& dev, int occ, MomentLaunch& L);
+// block-column mode: number of trailing axes forming a block of at most 16 elements
+// (0 = row mode; f64 always uses row mode)
+int moment_block_axes(const Canon& c, int dtype);
 
 // lane segment length chosen for the moment (exposed for the workspace bound)
 long long moment_segment(const Canon& c, int es, long long target_lanes);
