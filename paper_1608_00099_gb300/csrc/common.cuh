@@ -8,7 +8,7 @@
 namespace triot {
 
 constexpr int kMaxRank = 24;
-constexpr int kMomentWarps = 4;  // warps per CTA of the row-mode moment kernels
+constexpr int kMomentWarps = 4;     // warps per CTA of the row-mode moment kernels
 constexpr int kMomentBlkWarps = 2;  // warps per CTA of the block-column moment kernel
 
 enum RowOp { ROW_EMBED = 0, ROW_CROP = 1, ROW_PRODUCT = 2 };

@@ -391,12 +391,18 @@ __global__ void __launch_bounds__(kBlkWarps * 32) moment_blk_kernel(
       const unsigned char* row = stage[warp][s & 1] + lane * kStageRowBytes;
       const long long left = g.seg - (long long)chunk * C;
       const int cnt = left < C ? (int)left : C;
-#pragma unroll 4
-      for (int j = 0; j < cnt; ++j) {
-        const float x = elem_f32<T>(row, j);
-        cs[jb] += x;
-        bm += x;
-        if (++jb == B) {
+      // runs up to the next block end: the carry code has a single call site
+      int j = 0;
+      while (j < cnt) {
+        const int n = (B - jb) < (cnt - j) ? (B - jb) : (cnt - j);
+        for (int k = 0; k < n; ++k) {
+          const float x = elem_f32<T>(row, j + k);
+          cs[jb + k] += x;
+          bm += x;
+        }
+        j += n;
+        jb += n;
+        if (jb == B) {
           jb = 0;
           block_end();
         }

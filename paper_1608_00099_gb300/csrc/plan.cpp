@@ -310,6 +310,15 @@ void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const T
       const long long fill = (c.total / std::max(1ll, target_lanes)) / base * base;
       S = std::max(base, std::min(S, fill));
     }
+    // align segments to whole blocks of the innermost outer axes as far as S allows, so
+    // the lanes of a warp wrap those digits at the same step (carries without divergence)
+    long long align = B;
+    for (int a = D - m - 1; a >= 0; --a) {
+      if (align * c.ext[a] > S) break;
+      align *= c.ext[a];
+    }
+    const long long align2 = align / gcd_ll(align, al) * al;
+    if (S >= align2) S = S / align2 * align2;
     g.seg = S;
     g.nchunks = (int)((S + C - 1) / C);
   } else {
