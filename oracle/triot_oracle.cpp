@@ -209,7 +209,9 @@ struct NeumaierSum {
     else c += (v - t) + s;
     s = t;
   }
-  double value() const { return s + c; }
+  // Once the running sum is non-finite, the plain sum of Algorithms 10/11 is that value
+  // (inf, or NaN after inf - inf); the correction term (inf - inf there) carries nothing.
+  double value() const { return std::isfinite(s) ? s + c : s; }
 };
 
 // split [0, n) into `parts` contiguous ranges (the outer-axis partition of Section 4)

@@ -377,6 +377,27 @@ def test_moment_threads_match(orc):
     assert np.allclose(m1, m5, rtol=1e-15, atol=0)
 
 
+@pytest.mark.parametrize("nthreads", [1, 3])
+def test_moment_nonfinite_is_the_plain_ieee_sum(orc, nthreads):
+    """A non-finite weight gives what the plain f64 sum of p[t] * t_i gives (IEEE rules)."""
+    shape = (3, 4)
+    base = np.random.default_rng(25).random(12)
+    cases = [
+        ({(1, 2): np.inf}, [np.inf, np.inf, np.inf]),
+        ({(0, 2): np.inf}, [np.nan, np.inf, np.inf]),          # 0 * inf = NaN on axis 0
+        ({(2, 3): -np.inf}, [-np.inf, -np.inf, -np.inf]),
+        ({(1, 1): np.inf, (2, 2): -np.inf}, [np.nan, np.nan, np.nan]),
+        ({(1, 3): np.nan}, [np.nan, np.nan, np.nan]),
+    ]
+    for bad, want in cases:
+        p = base.copy().reshape(shape)
+        for t, v in bad.items():
+            p[t] = v
+        got = orc.moment(p.reshape(-1), shape, "f64", nthreads=nthreads)
+        for g_, w_ in zip(got, want):
+            assert (np.isnan(g_) and np.isnan(w_)) or g_ == w_, (bad, got)
+
+
 # ---------------------------------------------------------------- convolution (Alg 14)
 
 def test_convolution_against_scipy(orc):
