@@ -108,17 +108,27 @@ int launch_rows(int op, int rank, const int64_t* xshape, const void* x, const in
 }
 
 // ------------------------------------------------------------------ moment
-static int moment_occupancy(const void* fn, int threads, int& occ) {
+static int moment_occupancy(const void* fn, int threads, size_t dyn, size_t dyn_max, int& occ) {
+  struct Entry { const void* fn; size_t dyn; int dev; int occ; };
   static std::mutex mu;
-  static std::vector<std::pair<const void*, int>> table;
+  static std::vector<Entry> table;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   std::lock_guard<std::mutex> lk(mu);
-  for (const auto& kv : table)
-    if (kv.first == fn) { occ = kv.second; return TRIOT_OK; }
+  for (const auto& x : table)
+    if (x.fn == fn && x.dyn == dyn && x.dev == dev) { occ = x.occ; return TRIOT_OK; }
+  if (dyn > 0) {
+    // opt in to the largest dynamic shared memory any launch of this kernel can need (the
+    // attribute is per kernel, so it must cover every rank, not just this call's)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(max dynamic shared memory)");
+  }
   int o = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, dyn);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   occ = o > 0 ? o : 1;
-  table.emplace_back(fn, occ);
+  table.push_back({fn, dyn, dev, occ});
   return TRIOT_OK;
 }
 
@@ -132,12 +142,19 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
   DeviceInfo dev;
   if ((st = device_info(dev))) return st;
   const int m = moment_block_axes(c, dtype);
-  const void* fn = moment_kernel_ptr(dtype, c.D, m);
+  int B = 1;
+  for (int a = c.D - m; a < c.D; ++a) B *= (int)c.ext[a];
+  const void* fn = moment_kernel_ptr(dtype, c.D, m, B);
   if (!fn) return fail(TRIOT_ERR_RANK, "no moment kernel for this effective rank");
   int occ = 1;
-  if ((st = moment_occupancy(fn, (m > 0 ? kMomentBlkWarps : kMomentWarps) * 32, occ))) return st;
+  const bool b64 = m > 0 && dtype == DT_F64;
+  const size_t dyn = b64 ? (size_t)b64_dyn_smem(B, c.D - m) : 0;
+  const size_t dyn_max = b64 ? (size_t)b64_dyn_smem(B, kMaxRank - 1) : 0;
+  const int threads = (b64 ? kB64Warps : m > 0 ? kMomentBlkWarps : kMomentWarps) * 32;
+  if ((st = moment_occupancy(fn, threads, dyn, dyn_max, occ))) return st;
   TuneCfg t = force ? *force : tune_lookup(TRIOT_OP_MOMENT, dtype, c);
   plan_moment(c, rank, dtype_size(dtype), m, p, t, dev, occ, L);
+  L.smem = dyn;
   if (L.grid > kMaxMomentParts) return fail(TRIOT_ERR_ARG, "moment grid exceeds the partial limit");
   return TRIOT_OK;
 }
@@ -151,11 +168,11 @@ int launch_moment(const MomentLaunch& L, int dtype, const void* p, double* out, 
                   cudaStream_t stream) {
   cudaError_t e;
   if (!L.empty) {
-    const void* fn = moment_kernel_ptr(dtype, L.g.D, L.g.m);
+    const void* fn = moment_kernel_ptr(dtype, L.g.D, L.g.m, L.g.B);
     if (!fn) return fail(TRIOT_ERR_RANK, "no moment kernel for this effective rank");
     double* part = static_cast<double*>(ws);
     void* args[] = {(void*)&L.g, (void*)&p, (void*)&part};
-    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.warps * 32), args, 0, stream);
+    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.warps * 32), args, L.smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "moment kernel launch");
   }
   const double* partc = static_cast<const double*>(ws);
@@ -275,9 +292,10 @@ int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q
 int triot_device_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-  int flag = 0;
+  int flag = 0, flag2 = 0;
   st_read_device_flag(&flag);
-  return flag ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped") : ok();
+  b64_read_device_flag(&flag2);
+  return (flag || flag2) ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped") : ok();
 }
 
 }  // extern "C"

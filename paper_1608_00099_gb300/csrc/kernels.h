@@ -10,7 +10,11 @@ const void* crop_kernel_ptr(int es, int nouter);
 const void* product_kernel_ptr(int dtype, int nouter);
 // moment kernels by dtype and effective rank D in [1, 24]; m > 0 selects the block-column
 // kernel (f32/bf16/f16 only) with D - m outer axes
-const void* moment_kernel_ptr(int dtype, int D, int m = 0);
+// m > 0: block-column kernel for blocks of B elements (the last m axes)
+const void* moment_kernel_ptr(int dtype, int D, int m = 0, int B = 0);
 const void* moment_blk_kernel_ptr(int dtype, int DO);
+const void* moment_blk64_kernel_ptr(int B, int DO);
+// sticky flag of the f64 block kernel (a bounded wait gave up); reading clears it
+void b64_read_device_flag(int* flag);
 const void* combine_kernel_ptr();
 }  // namespace triot

@@ -592,6 +592,35 @@ __global__ void __launch_bounds__(kMomentWarps * 32, (D <= 12 ? 4 : 2)) moment_f
     }
   };
 
+  // Fast chunk: every element finite, non-negative and normal, exponents within 32 binades
+  // of the chunk maximum.  Then m >> sh needs two 32-bit funnel shifts and no sign or
+  // subnormal handling: about nine integer instructions per element.
+  auto do_chunk_fast = [&](const uint2* row2, uint32_t ec) {
+    int j = 0;
+    while (j < C) {
+      const int left = ti < L ? (int)(L - ti) : C;
+      const int n = left < C - j ? left : C - j;
+      unsigned long long Pr = 0, Q = 0;
+#pragma unroll 2
+      for (int k = 0; k < n; ++k) {
+        const uint2 b = row2[j + k];
+        const uint32_t sh = ec - (b.y >> 20);
+        const uint32_t mh = (b.y & 0x000FFFFFu) | 0x00100000u;
+        const uint32_t cl = __funnelshift_r(b.x, mh, sh);
+        const uint32_t ch = mh >> sh;
+        Pr += ((unsigned long long)ch << 32) | cl;
+        Q += Pr;
+      }
+      add_run((long long)Pr, (long long)((unsigned long long)n * Pr - Q), ti, (int)ec);
+      j += n;
+      ti += (uint32_t)n;
+      if (ti == L) {
+        ti = 0;
+        carry();
+      }
+    }
+  };
+
   if (nsteps > 0) {
     stage_chunk<ES>(g, pb, stage[warp][0], gw, 0, lane);
     cp_async_commit();
@@ -619,20 +648,34 @@ __global__ void __launch_bounds__(kMomentWarps * 32, (D <= 12 ? 4 : 2)) moment_f
     if (active) {
     const unsigned long long* row =
         reinterpret_cast<const unsigned long long*>(stage[warp][s & 1] + lane * kStageRowBytes);
-    // largest exponent field of the chunk (zeros and subnormals count as exponent 1)
-    uint32_t emaxf = 0x00100000u, efin = 0x00100000u;
+    // unsigned max / min of the high words: for non-negative values they order by exponent;
+    // a negative value (sign bit) or a non-finite one pushes the max to 0x7FF00000 or above,
+    // a zero or subnormal pulls the min below 0x00100000
+    uint32_t hmax = 0u, hmin = 0xFFFFFFFFu;
 #pragma unroll
     for (int j = 0; j < C; j += 2) {
       const uint4 v = *reinterpret_cast<const uint4*>(row + j);
-      const uint32_t f0 = v.y & 0x7FF00000u, f1 = v.w & 0x7FF00000u;
-      emaxf = max(emaxf, max(f0, f1));
-      efin = max(efin, max(f0 == 0x7FF00000u ? 0u : f0, f1 == 0x7FF00000u ? 0u : f1));
+      hmax = max(hmax, max(v.y, v.w));
+      hmin = min(hmin, min(v.y, v.w));
     }
-    if (emaxf != 0x7FF00000u) {
-      do_chunk(row, (int)(emaxf >> 20), std::false_type());
+    if (hmax < 0x7FF00000u && hmin >= 0x00100000u && (hmax >> 20) - (hmin >> 20) < 32u) {
+      do_chunk_fast(reinterpret_cast<const uint2*>(row), hmax >> 20);
     } else {
-      special = true;
-      do_chunk(row, (int)(efin >> 20), std::true_type());
+      // general chunk: largest finite exponent field (zeros and subnormals count as 1)
+      uint32_t emaxf = 0x00100000u, efin = 0x00100000u;
+#pragma unroll
+      for (int j = 0; j < C; j += 2) {
+        const uint4 v = *reinterpret_cast<const uint4*>(row + j);
+        const uint32_t f0 = v.y & 0x7FF00000u, f1 = v.w & 0x7FF00000u;
+        emaxf = max(emaxf, max(f0, f1));
+        efin = max(efin, max(f0 == 0x7FF00000u ? 0u : f0, f1 == 0x7FF00000u ? 0u : f1));
+      }
+      if (emaxf != 0x7FF00000u) {
+        do_chunk(row, (int)(emaxf >> 20), std::false_type());
+      } else {
+        special = true;
+        do_chunk(row, (int)(efin >> 20), std::true_type());
+      }
     }
     if (chunk == g.nchunks - 1) flush_levels();
     }

@@ -15,9 +15,12 @@ const void* pick(int d, std::integer_sequence<int, N...>) {
 }
 }  // namespace
 
-const void* moment_kernel_ptr(int dtype, int D, int m) {
+const void* moment_kernel_ptr(int dtype, int D, int m, int B) {
   if (D < 1 || D > kMaxRank) return nullptr;
-  if (m > 0) return (dtype == DT_F64 || m > D) ? nullptr : moment_blk_kernel_ptr(dtype, D - m);
+  if (m > 0) {
+    if (m > D) return nullptr;
+    return dtype == DT_F64 ? moment_blk64_kernel_ptr(B, D - m) : moment_blk_kernel_ptr(dtype, D - m);
+  }
   auto seq = std::make_integer_sequence<int, kMaxRank>{};
   switch (dtype) {
     case DT_F64: return moment_f64_ptr(D);

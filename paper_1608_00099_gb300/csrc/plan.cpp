@@ -265,7 +265,7 @@ long long moment_segment(const Canon& c, int es, long long target_lanes) {
 }
 
 int moment_block_axes(const Canon& c, int dtype) {
-  if (dtype == DT_F64) return 0;
+  (void)dtype;
   long long b = 1;
   int m = 0;
   for (int a = c.D - 1; a >= 0; --a) {
@@ -291,12 +291,23 @@ void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const T
   g.aligned = (reinterpret_cast<uintptr_t>(p) % 16) == 0;
   const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
   const long long max_ctas = (long long)dev.sms * std::max(1, cps);
-  const int warps = m > 0 ? kMomentBlkWarps : kMomentWarps;
+  const int warps = (m > 0 && es == 8) ? kB64Warps : m > 0 ? kMomentBlkWarps : kMomentWarps;
   L.warps = warps;
   const long long target_lanes = max_ctas * warps * 32;
   const long long C = 128 / es;
   g.m = m;
-  if (m > 0) {
+  if (m > 0 && es == 8) {
+    // f64 blocks: rounds of 32 chunks of K whole blocks each; every warp takes a contiguous
+    // share of the rounds (the kernel splits them evenly), one chunk per lane and round
+    long long B = 1;
+    for (int a = D - m; a < D; ++a) B *= c.ext[a];
+    g.B = (int)B;
+    const long long CB = (long long)b64_blocks_per_chunk((int)B) * B;
+    g.seg = CB;
+    g.nchunks = 1;
+    g.nround = (c.total + 32 * CB - 1) / (32 * CB);
+    g.win = (int)std::max(1ll, kB64Window / CB);
+  } else if (m > 0) {
     long long B = 1;
     for (int a = D - m; a < D; ++a) B *= c.ext[a];
     g.B = (int)B;

@@ -43,13 +43,14 @@ struct MomentLaunch {
   CombineGeom cg;
   int grid = 0;        // CTAs of the moment kernel (= number of partial vectors)
   int warps = 4;       // warps per CTA
+  size_t smem = 0;     // dynamic shared memory per CTA (f64 block kernel: outer-axis state)
   bool empty = false;  // nothing to sum: only the combine runs (it writes zeros)
 };
 // `occ` = resident CTAs per SM of the chosen kernel (from the occupancy calculator).
 void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
                  const DeviceInfo& dev, int occ, MomentLaunch& L);
 // block-column mode: number of trailing axes forming a block of at most 16 elements
-// (0 = row mode; f64 always uses row mode)
+// (0 = row mode, for inner extents above 16)
 int moment_block_axes(const Canon& c, int dtype);
 
 // lane segment length chosen for the moment (exposed for the workspace bound)
