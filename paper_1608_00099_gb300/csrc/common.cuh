@@ -20,17 +20,17 @@ __host__ __device__ constexpr int b64_blocks_per_chunk(int b) {
 // f64 block kernel: warps per CTA, staged rounds per warp, bytes of one lane row of a stage
 // (an odd number of 16-byte units: conflict-free 16-byte reads across lanes), and its dynamic
 // shared memory: the stages, then lane-major per-axis state (128-bit axis sums and 32-bit
-// digits of axes 0..DO-3, 128-bit pending masses of axes 0..DO-4, and the lane's f64 totals
+// digits of axes 0..DO-4, 128-bit pending masses of axes 0..DO-5, and the lane's f64 totals
 // of axes 0..DO-1)
 constexpr int kB64Warps = 2;
 constexpr int kB64Stages = 2;
-constexpr int kB64Window = 512;  // elements a lane sums in one fixed-point window
+constexpr int kB64Window = 1024;  // elements a lane sums in one fixed-point window
 __host__ __device__ constexpr int b64_row_bytes(int b) {
   return b64_blocks_per_chunk(b) * b * 8 + (((b64_blocks_per_chunk(b) * b / 2) & 1) ? 0 : 16);
 }
 __host__ __device__ constexpr int b64_stage_bytes(int b) { return kB64Warps * kB64Stages * 32 * b64_row_bytes(b); }
-__host__ __device__ constexpr int b64_levels(int DO) { return DO >= 3 ? DO - 2 : 0; }
-__host__ __device__ constexpr int b64_qlevels(int DO) { return DO >= 4 ? DO - 3 : 0; }
+__host__ __device__ constexpr int b64_levels(int DO) { return DO >= 4 ? DO - 3 : 0; }
+__host__ __device__ constexpr int b64_qlevels(int DO) { return DO >= 5 ? DO - 4 : 0; }
 __host__ __device__ constexpr int b64_dyn_smem(int b, int DO) {
   return b64_stage_bytes(b) +
          kB64Warps * 32 * (b64_levels(DO) * 20 + b64_qlevels(DO) * 16 + DO * 8);

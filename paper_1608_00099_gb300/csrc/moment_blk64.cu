@@ -16,14 +16,17 @@
 // E_W grows).  Per lane and window:
 //   * column sums cs[j] (64-bit, one register pair per column; B is a template parameter),
 //     which give the block axes' moments sum_j cs[j] * digit_a(j) at the window end;
-//   * the two innermost outer axes summed eagerly per block (A1 += bm * t1, A2 += bm * t2,
-//     bm the block's mass), so their digits may differ between lanes without divergence;
-//   * the remaining outer axes summed lazily: a block's mass waits in the pending mass of
-//     axis DO-3 and is credited (A_i += pending * t_i) only when t_i changes, then moves up.
+//   * the three innermost outer axes summed eagerly once per chunk from its block masses:
+//     the chunk's K blocks cross at most one wrap of axis DO-1 (when K <= its extent), so
+//     they split into two runs with fixed digits, and A1 += t1 * M + sum_k k bm_k - E1 * Mb,
+//     A2 += t2 * Ma + t2' * Mb, A3 likewise (M = Ma + Mb the masses before and after the
+//     wrap); lanes with different digits run the same instructions;
+//   * the remaining outer axes summed lazily: a chunk's mass waits in the pending mass of
+//     axis DO-4 and is credited (A_i += pending * t_i) only when t_i changes, then moves up.
 // At the window end the sums are rounded once to f64 and added to the lane's f64 totals.
 // Truncation below the window maximum's last bit bounds the error of every output by
 // 2^-52 * max|p| (over the window) per element; relative to sum |p| t_i that is at most
-// kB64Window * 2^-52 (1.1e-13), and for data of similar magnitudes near 2^-52.  Non-finite
+// kB64Window * 2^-52 (2.3e-13), and for data of similar magnitudes near 2^-52.  Non-finite
 // elements are summed separately in f64 so that they propagate as they would in a plain sum.
 #include <utility>
 
@@ -112,12 +115,14 @@ struct LaneCol {
 };
 
 // non-finite element: plain f64 sums of v * t_i (rare; kept out of line)
-__device__ __noinline__ void add_special(double v, uint32_t t1, uint32_t t2, LaneCol<uint32_t> tc,
-                                         int DO, int m, const unsigned char* dig_j, double* Asp,
-                                         double* Isp, double* Psp) {
+__device__ __noinline__ void add_special(double v, uint32_t t1, uint32_t t2, uint32_t t3,
+                                         LaneCol<uint32_t> tc, int DO, int m,
+                                         const unsigned char* dig_j, double* Asp, double* Isp,
+                                         double* Psp) {
   if (DO >= 1) Asp[DO - 1] += v * (double)t1;
   if (DO >= 2) Asp[DO - 2] += v * (double)t2;
-  for (int i = 0; i + 2 < DO; ++i) Asp[i] += v * (double)tc[i];
+  if (DO >= 3) Asp[DO - 3] += v * (double)t3;
+  for (int i = 0; i + 3 < DO; ++i) Asp[i] += v * (double)tc[i];
   for (int a = 0; a < m; ++a) Isp[a] += v * (double)dig_j[a * 16];
   *Psp += v;
 }
@@ -176,12 +181,16 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
   const long long r0 = g.nround * gw / W, r1 = g.nround * (gw + 1) / W;  // this warp's rounds
   const long long nbytes = g.n * 8;
   const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
-  const uint32_t E1 = DO >= 2 ? (uint32_t)g.ext[DO - 1] : 0xFFFFFFFFu;  // innermost outer axis
-  const uint32_t E2 = DO >= 3 ? (uint32_t)g.ext[DO - 2] : 0xFFFFFFFFu;  // the next one
+  // extents of axes DO-1, DO-2, DO-3 (the outermost axis never wraps inside the tensor)
+  const uint32_t E1 = DO >= 2 ? (uint32_t)g.ext[DO - 1] : 0xFFFFFFFFu;
+  const uint32_t E2 = DO >= 3 ? (uint32_t)g.ext[DO - 2] : 0xFFFFFFFFu;
+  const uint32_t E3 = DO >= 4 ? (uint32_t)g.ext[DO - 3] : 0xFFFFFFFFu;
   const uint32_t j1 = DO >= 1 ? s_jd[DO - 1] : 0u;
   const uint32_t j2 = DO >= 2 ? s_jd[DO - 2] : 0u;
-  bool jcold = false;  // the jump changes a digit above axis DO-2 by itself
-  for (int i = 0; i + 2 < DO; ++i) jcold = jcold || s_jd[i] != 0u;
+  const uint32_t j3 = DO >= 3 ? s_jd[DO - 3] : 0u;
+  bool jcold = false;  // the jump changes a digit above axis DO-3 by itself
+  for (int i = 0; i + 3 < DO; ++i) jcold = jcold || s_jd[i] != 0u;
+  const bool per_round = (uint32_t)K <= E1;  // a chunk crosses at most one wrap of axis DO-1
 
   // round r (32 chunks, contiguous) into stage q.  Dense rows (PAD == 0) of an aligned,
   // complete round: one bulk copy issued by lane 0, completing on the stage's mbarrier.
@@ -254,14 +263,14 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
 
   // ---- lane state (window sums in fixed point)
   long long cs[B];                      // column sums
-  __int128 A1 = 0, A2 = 0;              // axes DO-1 and DO-2: sum of block mass * digit
-  __int128 Q3 = 0;                      // mass not yet credited to axis DO-3 (or the mass)
+  __int128 A1 = 0, A2 = 0, A3 = 0;      // axes DO-1, DO-2, DO-3: sum of mass * digit
+  __int128 Q4 = 0;                      // mass not yet credited to axis DO-4 (or the mass)
   __int128 Mtot = 0;                    // mass that left the outermost level
-  uint32_t t1 = 0, t2 = 0;              // digits of axes DO-1 and DO-2
+  uint32_t t1 = 0, t2 = 0, t3 = 0;      // digits of axes DO-1, DO-2, DO-3
   int es = 0;                           // window exponent (0: nothing seen)
 #pragma unroll
   for (int j = 0; j < B; ++j) cs[j] = 0;
-  // axes 0 .. DO-3 and the lane's f64 totals: lane-major dynamic shared memory after the
+  // axes 0 .. DO-4 and the lane's f64 totals: lane-major dynamic shared memory after the
   // stages (touched at carries and window ends; run-time axis index)
   unsigned char* st_base = dsm + (size_t)b64_stage_bytes(B);
   const LaneCol<__int128> Ac{reinterpret_cast<__int128*>(st_base) + threadIdx.x};
@@ -286,21 +295,22 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
       for (int j = 0; j < B; ++j) cs[j] = shr64(cs[j], d);
       A1 = shr_arith(A1, d);
       A2 = shr_arith(A2, d);
-      Q3 = shr_arith(Q3, d);
+      A3 = shr_arith(A3, d);
+      Q4 = shr_arith(Q4, d);
       Mtot = shr_arith(Mtot, d);
       for (int i = 0; i < b64_levels(DO); ++i) Ac[i] = shr_arith(Ac[i], d);
       for (int i = 0; i < b64_qlevels(DO); ++i) Qc[i] = shr_arith(Qc[i], d);
     }
     es = e_new;
   };
-  // digits of axes DO-3 .. 0 advance by inc_i = (jump digit if `jump`) + carry.  Every axis
+  // digits of axes DO-4 .. 0 advance by inc_i = (jump digit if `jump`) + carry.  Every axis
   // up to the outermost one that changes first hands its pending mass to the axis above
   // (crediting it with its current digit), so no mass is ever credited with a wrong digit.
   auto cold_step = [&](uint32_t carry_in, bool jump) {
     int h = -1;  // outermost changing axis
     {
       uint32_t carry = carry_in;
-      for (int i = DO - 3; i >= 0; --i) {
+      for (int i = DO - 4; i >= 0; --i) {
         const uint32_t inc = (jump ? s_jd[i] : 0u) + carry;
         if (inc) h = i;
         carry = (i > 0 && tc[i] + inc >= (uint32_t)g.ext[i]) ? 1u : 0u;
@@ -309,9 +319,9 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
     }
     if (h < 0) return;
     uint32_t carry = carry_in;
-    __int128 pend = Q3;
-    Q3 = 0;
-    for (int i = DO - 3; i >= h; --i) {
+    __int128 pend = Q4;
+    Q4 = 0;
+    for (int i = DO - 4; i >= h; --i) {
       const uint32_t t = tc[i];
       mac128x32(Ac[i], pend, t);
       if (i > 0) {
@@ -331,33 +341,93 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
     }
     if (h > 0) Qc[h - 1] += pend;
   };
+  // from a chunk's last block to the lane's first block of its next round
+  auto jump = [&]() {
+    t1 += j1;
+    const uint32_t c1 = t1 >= E1 ? 1u : 0u;
+    t1 -= c1 ? E1 : 0u;
+    t2 += j2 + c1;
+    const uint32_t c2 = t2 >= E2 ? 1u : 0u;
+    t2 -= c2 ? E2 : 0u;
+    t3 += j3 + c2;
+    const uint32_t c3 = t3 >= E3 ? 1u : 0u;
+    t3 -= c3 ? E3 : 0u;
+    if (c3 || jcold) cold_step(c3, jcold);
+  };
+  // one block at a time (chunks with non-finite or unusual elements, or K > E1)
   auto block_end = [&](long long bm, bool last_in_chunk) {
     mac64x32(A1, bm, t1);
     if (DO >= 2) mac64x32(A2, bm, t2);
-    Q3 += bm;
-    uint32_t c2;
+    if (DO >= 3) mac64x32(A3, bm, t3);
+    Q4 += bm;
     if (!last_in_chunk) {
       const uint32_t w1 = (++t1 == E1) ? 1u : 0u;
       t1 = w1 ? 0u : t1;
       t2 += w1;
-      c2 = (t2 == E2) ? 1u : 0u;
-      t2 = c2 ? 0u : t2;
-      if (c2) cold_step(1u, false);
+      const uint32_t w2 = (t2 == E2) ? 1u : 0u;
+      t2 = w2 ? 0u : t2;
+      t3 += w2;
+      const uint32_t w3 = (t3 == E3) ? 1u : 0u;
+      t3 = w3 ? 0u : t3;
+      if (w3) cold_step(1u, false);
     } else {
-      t1 += j1;
-      const uint32_t c1 = t1 >= E1 ? 1u : 0u;
-      t1 -= c1 ? E1 : 0u;
-      t2 += j2 + c1;
-      c2 = t2 >= E2 ? 1u : 0u;
-      t2 -= c2 ? E2 : 0u;
-      if (c2 || jcold) cold_step(c2, jcold);
+      jump();
     }
+  };
+  // a whole chunk from its K block masses (K <= E1: at most one wrap of axis DO-1, after
+  // block kw = E1 - t1); then the jump to the next round
+  auto chunk_end = [&](const long long (&bmv)[K]) {
+    long long M = 0, Wk = 0, Mb = 0;
+    const uint32_t kw = E1 - t1;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      M += bmv[k];
+      Wk += (long long)k * bmv[k];
+      Mb += ((uint32_t)k >= kw) ? bmv[k] : 0ll;
+    }
+    const long long Ma = M - Mb;
+    const bool wrap1 = kw < (uint32_t)K;
+    uint32_t t2b = t2, t3b = t3;
+    bool c3 = false;
+    if (wrap1) {
+      t2b = t2 + 1;
+      if (t2b == E2) {
+        t2b = 0;
+        t3b = t3 + 1;
+        if (t3b == E3) {
+          t3b = 0;
+          c3 = true;
+        }
+      }
+    }
+    mac64x32(A1, M, t1);
+    A1 += Wk;
+    mac64x32(A1, -Mb, E1);
+    if (DO >= 2) {
+      mac64x32(A2, Ma, t2);
+      mac64x32(A2, Mb, t2b);
+    }
+    if (DO >= 3) {
+      mac64x32(A3, Ma, t3);
+      mac64x32(A3, Mb, t3b);
+    }
+    if (!c3) {
+      Q4 += M;
+    } else {
+      Q4 += Ma;
+      cold_step(1u, false);
+      Q4 += Mb;
+    }
+    t1 = t1 + (uint32_t)(K - 1) - (wrap1 ? E1 : 0u);
+    t2 = t2b;
+    t3 = t3b;
+    jump();
   };
   // window end: credit every pending mass, round the window's sums to f64 once
   auto end_window = [&]() {
-    __int128 pend = Q3;
-    Q3 = 0;
-    for (int i = DO - 3; i >= 0; --i) {
+    __int128 pend = Q4;
+    Q4 = 0;
+    for (int i = DO - 4; i >= 0; --i) {
       mac128x32(Ac[i], pend, tc[i]);
       if (i > 0) {
         pend += Qc[i - 1];
@@ -369,7 +439,8 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
       const int sc = es - 1075;
       if (DO >= 1) Ads[DO - 1] += fixed_to_double(A1, sc);
       if (DO >= 2) Ads[DO - 2] += fixed_to_double(A2, sc);
-      for (int i = 0; i + 2 < DO; ++i) Ads[i] += fixed_to_double(Ac[i], sc);
+      if (DO >= 3) Ads[DO - 3] += fixed_to_double(A3, sc);
+      for (int i = 0; i + 3 < DO; ++i) Ads[i] += fixed_to_double(Ac[i], sc);
       Md += fixed_to_double(Mtot, sc);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -384,6 +455,7 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
     for (int j = 0; j < B; ++j) cs[j] = 0;
     A1 = 0;
     A2 = 0;
+    A3 = 0;
     Mtot = 0;
     for (int i = 0; i < b64_levels(DO); ++i) Ac[i] = 0;
     es = 0;
@@ -391,52 +463,30 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
 
   const long long nsteps = r1 - r0;
   if (nsteps > 0) {
-    // tuple of this lane's first block
+    // tuple of this lane's first block (the outermost axis takes the remainder)
     const long long blk = (r0 * 32 + lane) * K;
+    auto set_digit = [&](int a, uint32_t v) {
+      if (a == DO - 1) t1 = v;
+      else if (a == DO - 2) t2 = v;
+      else if (a == DO - 3) t3 = v;
+      else tc[a] = v;
+    };
     if (g.n32) {
       uint32_t r32 = (uint32_t)blk;
-      if (DO >= 2) {
-        const uint32_t q = fdiv(r32, g.div[DO - 1]);
-        t1 = r32 - q * g.div[DO - 1].d;
+      for (int a = DO - 1; a >= 1; --a) {
+        const uint32_t q = fdiv(r32, g.div[a]);
+        set_digit(a, r32 - q * g.div[a].d);
         r32 = q;
-        if (DO >= 3) {
-          const uint32_t q2 = fdiv(r32, g.div[DO - 2]);
-          t2 = r32 - q2 * g.div[DO - 2].d;
-          r32 = q2;
-          for (int i = DO - 3; i >= 1; --i) {
-            const uint32_t q3 = fdiv(r32, g.div[i]);
-            tc[i] = r32 - q3 * g.div[i].d;
-            r32 = q3;
-          }
-          tc[0] = r32;
-        } else {
-          t2 = r32;
-        }
-      } else {
-        t1 = r32;
       }
+      if (DO >= 1) set_digit(0, r32);
     } else {
       long long q = blk;
-      if (DO >= 2) {
-        long long q1 = q / g.ext[DO - 1];
-        t1 = (uint32_t)(q - q1 * g.ext[DO - 1]);
+      for (int a = DO - 1; a >= 1; --a) {
+        const long long q1 = q / g.ext[a];
+        set_digit(a, (uint32_t)(q - q1 * g.ext[a]));
         q = q1;
-        if (DO >= 3) {
-          long long q2 = q / g.ext[DO - 2];
-          t2 = (uint32_t)(q - q2 * g.ext[DO - 2]);
-          q = q2;
-          for (int i = DO - 3; i >= 1; --i) {
-            const long long q3 = q / g.ext[i];
-            tc[i] = (uint32_t)(q - q3 * g.ext[i]);
-            q = q3;
-          }
-          tc[0] = (uint32_t)q;
-        } else {
-          t2 = (uint32_t)q;
-        }
-      } else {
-        t1 = (uint32_t)q;
       }
+      if (DO >= 1) set_digit(0, (uint32_t)q);
     }
   }
 
@@ -444,7 +494,9 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
 #pragma unroll
   for (int q = 0; q < NS - 1; ++q)
     if (ri < r1) stage_round(ri++, q);
-  int buf = 0, wpos = 0;
+  // window phases staggered across warps, so that the window ends (a burst of work with no
+  // copy in flight) of the warps sharing an SM do not coincide
+  int buf = 0, wpos = (int)(gw % g.win);
   for (long long s = 0; s < nsteps; ++s) {
     wait_stage(buf);
     __syncwarp();
@@ -483,7 +535,8 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
     }
     const uint32_t ec = (uint32_t)es;
     if (clean && ec - (hmin >> 20) < 32u) {
-      long long cb[B];  // the block's elements; its mass is their sum taken as a tree
+      long long cb[B];   // the block's elements; its mass is their sum taken as a tree
+      long long bmv[K];  // the chunk's block masses
 #pragma unroll
       for (int idx = 0; idx < CB; idx += 2) {
         const uint4 v = *reinterpret_cast<const uint4*>(row + 8 * idx);
@@ -502,9 +555,15 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
             for (int w = 1; w < B; w *= 2)
 #pragma unroll
               for (int q = 0; q + w < B; q += 2 * w) cb[q] += cb[q + w];
-            block_end(cb[0], idx + h == CB - 1);
+            bmv[(idx + h) / B] = cb[0];
           }
         }
+      }
+      if (per_round) {
+        chunk_end(bmv);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) block_end(bmv[k], k == K - 1);
       }
     } else {
       long long bm = 0;
@@ -520,7 +579,7 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
             for (int i = 0; i < DO; ++i) Asp[i] = 0.0;
             special = true;
           }
-          add_special(__longlong_as_double((long long)b), t1, t2, tc, DO, m, &s_dig[0][j], Asp,
+          add_special(__longlong_as_double((long long)b), t1, t2, t3, tc, DO, m, &s_dig[0][j], Asp,
                       Isp, &Psp);
         } else {
           const uint32_t e = (ef > 0x00100000u ? ef : 0x00100000u) >> 20;
@@ -545,13 +604,40 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
     __syncwarp();
   }
 
-  // warp reduction of the lane totals (f64, fixed xor order), then the CTA sum
+  // warp sum of the lane totals: exact in 128-bit fixed point relative to the warp's largest
+  // exponent (integer shuffles; the narrow FP64 pipe is left alone), or an f64 xor-order sum
+  // when a lane holds a non-finite value
   double* ws_out = wsum[warp];
   auto reduce_out = [&](double v, double sp, int slot) {
     if (special) v += sp;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    int e = (int)((bits >> 52) & 0x7FFull);
+    if (__any_sync(0xffffffffu, e == 0x7FF)) {
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) ws_out[slot] = v;
+      for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) ws_out[slot] = v;
+      return;
+    }
+    unsigned long long mant = bits & 0x000FFFFFFFFFFFFFull;
+    if (e) mant |= 1ull << 52;
+    else e = 1;
+    const int ew = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+    const int d = ew - e;  // v = mant * 2^(e - 1075) = (mant << (64 - d)) * 2^(ew - 1139)
+    __int128 x = 0;
+    if (d <= 64) x = (__int128)((unsigned __int128)mant << (64 - d));
+    else if (d < 64 + 53) x = (__int128)(mant >> (d - 64));
+    if (bits >> 63) x = -x;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const unsigned __int128 u = (unsigned __int128)x;
+      const unsigned w0 = __shfl_xor_sync(0xffffffffu, (unsigned)u, off);
+      const unsigned w1 = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 32), off);
+      const unsigned w2 = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 64), off);
+      const unsigned w3 = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 96), off);
+      x += (__int128)(((unsigned __int128)w3 << 96) | ((unsigned __int128)w2 << 64) |
+                      ((unsigned __int128)w1 << 32) | (unsigned __int128)w0);
+    }
+    if (lane == 0) ws_out[slot] = fixed_to_double(x, ew - 1139);
   };
   for (int i = 0; i < DO; ++i) reduce_out(Ads[i], special ? Asp[i] : 0.0, i);
 #pragma unroll

@@ -306,7 +306,9 @@ void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const T
     g.seg = CB;
     g.nchunks = 1;
     g.nround = (c.total + 32 * CB - 1) / (32 * CB);
-    g.win = (int)std::max(1ll, kB64Window / CB);
+    // a window: at most kB64Window elements per lane and 512 per block column (a column sum
+    // of 512 elements below 2^53 stays below 2^62)
+    g.win = (int)std::max(1ll, std::min((long long)kB64Window, 512 * B) / CB);
   } else if (m > 0) {
     long long B = 1;
     for (int a = D - m; a < D; ++a) B *= c.ext[a];
