@@ -48,6 +48,8 @@ def load(path: str):
     L.oracle_product_window.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p,
                                         C.c_uint64, C.c_uint64, C.c_void_p]
     L.oracle_moment.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, C.POINTER(C.c_double), C.c_int]
+    L.oracle_moment_product.argtypes = [C.c_int, C.c_uint, C.c_uint, _u64p, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_double)]
     L.oracle_convolve_f64.argtypes = [C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, C.c_void_p]
     return L
 
@@ -200,6 +202,22 @@ def moment(p: np.ndarray, shape, dtype: str, nthreads: int = 1) -> np.ndarray:
     out = np.zeros(len(s) + 1, dtype=np.float64)
     lib().oracle_moment(DTYPES[dtype], len(s), _p(s), _buf(p),
                         out.ctypes.data_as(C.POINTER(C.c_double)), nthreads)
+    return out
+
+
+def moment_product(tensors, shapes, dtype: str) -> np.ndarray:
+    """Moment of w = x_0 * x_1 * ... over the intersection of the shapes (Alg 11 with several
+    weight tensors): d+1 float64 [sum w*t_0, ..., sum w*t_{d-1}, sum w]."""
+    d = len(shapes[0])
+    assert all(len(s) == d for s in shapes) and len(tensors) == len(shapes) >= 1
+    flat = [np.ascontiguousarray(x).reshape(-1) for x in tensors]
+    for x, s in zip(flat, shapes):
+        _check(x, dtype, int(np.prod(s)))
+    allshapes = np.ascontiguousarray(np.concatenate([_shape(s) for s in shapes]))
+    ptrs = (C.c_void_p * len(flat))(*[x.ctypes.data for x in flat])
+    out = np.zeros(d + 1, dtype=np.float64)
+    lib().oracle_moment_product(DTYPES[dtype], d, len(flat), _p(allshapes), ptrs,
+                                out.ctypes.data_as(C.POINTER(C.c_double)))
     return out
 
 

@@ -461,6 +461,49 @@ void oracle_moment(int dtype, unsigned dim, const u64* shape, const void* p, dou
 
 // ------------------------------------------------------------------ convolution
 
+// The moment of a product of tensors over the intersection I of their shapes (Algorithm
+// 11 weights the tuple by x[t]*y[t]*z[t]; with two tensors the mass is benchmark 2's inner
+// product over the tuples both shapes share, Section 3):
+//   out[i]   = sum over t in I of w[t] * t_i,  i = 0..dim-1 (zero-based tuples),
+//   out[dim] = sum over t in I of w[t],        w[t] = x_0[t] * x_1[t] * ... * x_{n-1}[t].
+// w is formed left to right, each multiply rounded to nearest even in double for f64
+// tensors and in float for f32, bf16 and f16 tensors (whose values float holds exactly).
+// `shapes` holds n shapes of `dim` extents each, tensor k's at shapes[k*dim].  The tuples
+// of I are walked with Algorithm 3 and each tensor is addressed by Horner's rule
+// (Algorithm 2) with its own shape; sums are Neumaier-compensated in f64.
+void oracle_moment_product(int dtype, unsigned dim, unsigned n, const u64* shapes,
+                           const void* const* ptrs, double* out) {
+  for (unsigned i = 0; i <= dim; ++i) out[i] = 0.0;
+  if (n == 0) return;
+  std::vector<u64> I(dim);
+  for (unsigned i = 0; i < dim; ++i) {
+    I[i] = shapes[i];
+    for (unsigned k = 1; k < n; ++k) I[i] = shapes[k * dim + i] < I[i] ? shapes[k * dim + i] : I[i];
+  }
+  const u64 count = count_of(I.data(), dim);
+  if (count == 0) return;
+  std::vector<NeumaierSum> acc(dim + 1);
+  std::vector<u64> t(dim, 0);
+  for (u64 c = 0; c < count; ++c) {
+    double w;
+    if (dtype == T_F64) {
+      w = load_as_double(ptrs[0], tuple_to_index(t.data(), shapes, dim), dtype);
+      for (unsigned k = 1; k < n; ++k)
+        w = w * load_as_double(ptrs[k], tuple_to_index(t.data(), shapes + k * dim, dim), dtype);
+    } else {
+      float wf = float(load_as_double(ptrs[0], tuple_to_index(t.data(), shapes, dim), dtype));
+      for (unsigned k = 1; k < n; ++k)
+        wf = wf * float(load_as_double(ptrs[k], tuple_to_index(t.data(), shapes + k * dim, dim), dtype));
+      w = double(wf);
+    }
+    for (unsigned i = 0; i < dim; ++i) acc[i].add(w * double(t[i]));
+    acc[dim].add(w);
+    advance_tuple(t.data(), I.data(), dim);
+  }
+  for (unsigned i = 0; i <= dim; ++i) out[i] = acc[i].value();
+}
+
+
 // Naive multidimensional convolution by tuple iteration (Algorithm 14): for every pair of
 // tuples (a of lhs, b of rhs) add lhs[a]*rhs[b] into result[a + b]; result shape is
 // lhs.shape + rhs.shape - 1.  f64 only; plain (uncompensated) f64 adds in the paper's

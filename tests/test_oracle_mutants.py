@@ -38,6 +38,9 @@ MUTANTS = [
      [lambda o: pins.test_moment_point_mass_is_the_tuple(o, (3, 4))]),
     ("moment drops the mass term", "acc[dim].add(v);", "acc[dim].add(0.0);",
      [lambda o: pins.test_moment_constant_closed_form(o, (3, 4))]),
+    ("product moment addresses every tensor with the first shape",
+     "tuple_to_index(t.data(), shapes + k * dim, dim)", "tuple_to_index(t.data(), shapes, dim)",
+     [lambda o: pins.test_moment_product_brute_force_f64(o, 0)]),
     ("bf16 product rounds with f16 parameters",
      "yy[iy] = uint16_t(round_to_format(exact, 8, -126, 127, 8));",
      "yy[iy] = uint16_t(round_to_format(exact, 11, -14, 15, 5));",

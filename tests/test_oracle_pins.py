@@ -398,6 +398,94 @@ def test_moment_nonfinite_is_the_plain_ieee_sum(orc, nthreads):
             assert (np.isnan(g_) and np.isnan(w_)) or g_ == w_, (bad, got)
 
 
+# ---------------------------------------------------------------- moment of a product (Alg 11, n-ary)
+
+MP_CASES = [
+    [(3, 4), (5, 2)],
+    [(2, 3, 4), (2, 3, 4)],
+    [(4, 1, 3), (2, 5, 3), (3, 2, 2)],
+    [(2, 2, 2, 2), (3, 1, 2, 5), (2, 2, 1, 2), (2, 3, 2, 2)],
+    [(7,)],
+    [(1, 1, 3), (2, 2, 2)],
+]
+
+
+def _brute_product_moment(xs, shapes, ftype):
+    """numpy brute force: w over I (left-to-right products in ftype), exact f64 sums."""
+    import math
+    I = tuple(min(s[i] for s in shapes) for i in range(len(shapes[0])))
+    sl = tuple(slice(0, e) for e in I)
+    w = np.asarray(xs[0], dtype=np.float64).reshape(shapes[0])[sl].astype(ftype)
+    for x, s in zip(xs[1:], shapes[1:]):
+        w = (w * np.asarray(x, dtype=np.float64).reshape(s)[sl].astype(ftype)).astype(ftype)
+    w = w.astype(np.float64)
+    idx = np.indices(I) if len(I) else np.zeros((0,))
+    m = [math.fsum((w * idx[i]).ravel()) for i in range(len(I))]
+    return np.array(m + [math.fsum(w.ravel())])
+
+
+@pytest.mark.parametrize("case", range(len(MP_CASES)))
+def test_moment_product_brute_force_f64(orc, case):
+    shapes = MP_CASES[case]
+    rng = np.random.default_rng(40 + case)
+    xs = [rng.standard_normal(int(np.prod(s))) for s in shapes]
+    got = orc.moment_product(xs, shapes, "f64")
+    want = _brute_product_moment(xs, shapes, np.float64)
+    assert np.allclose(got, want, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_moment_product_float_products(orc, dtype):
+    """Sub-f64 tensors: w is the float32 product chain of the exactly decoded values."""
+    shapes = [(3, 5, 4), (4, 3, 6), (3, 4, 5)]
+    rng = np.random.default_rng(50)
+    xs = [orc.from_f64(rng.random(int(np.prod(s))) + 0.5, dtype) for s in shapes]
+    dec = [orc.to_f64(x, dtype) for x in xs]
+    got = orc.moment_product(xs, shapes, dtype)
+    want = _brute_product_moment(dec, shapes, np.float32)
+    assert np.allclose(got, want, rtol=1e-14, atol=0)
+
+
+def test_moment_product_inner_product(orc):
+    """Two tensors: the mass is the inner product over the tuples both shapes share."""
+    xs_shape, ys_shape = (6, 7, 5), (4, 9, 5)
+    rng = np.random.default_rng(51)
+    x = rng.random(int(np.prod(xs_shape)))
+    y = rng.random(int(np.prod(ys_shape)))
+    got = orc.moment_product([x, y], [xs_shape, ys_shape], "f64")
+    xa = x.reshape(xs_shape)[:4, :7, :5].ravel()
+    ya = y.reshape(ys_shape)[:4, :7, :5].ravel()
+    assert got[-1] == pytest.approx(float(np.dot(xa, ya)), rel=1e-14)
+
+
+def test_moment_product_ones_closed_form(orc):
+    """All-ones tensors: w = 1 on I, m_i = |I| (I_i - 1) / 2 exactly, mass |I|."""
+    shapes = [(5, 6, 3, 4), (7, 4, 3, 9), (5, 5, 8, 4)]
+    I = (5, 4, 3, 4)
+    xs = [np.ones(int(np.prod(s))) for s in shapes]
+    got = orc.moment_product(xs, shapes, "f64")
+    n = int(np.prod(I))
+    assert list(got) == [n * (e - 1) / 2 for e in I] + [float(n)]
+
+
+def test_moment_product_separable_closed_form(orc):
+    """x = a (x) b and y = c (x) d: w = (a c) (x) (b d) on I, so the moment factorises."""
+    rng = np.random.default_rng(52)
+    a, b, c, d = rng.random(6), rng.random(4), rng.random(5), rng.random(7)
+    x = np.outer(a, b).ravel()
+    y = np.outer(c, d).ravel()
+    got = orc.moment_product([x, y], [(6, 4), (5, 7)], "f64")
+    u, v = a[:5] * c, b[:4] * d[:4]
+    want = [np.sum(np.arange(5) * u) * v.sum(), u.sum() * np.sum(np.arange(4) * v), u.sum() * v.sum()]
+    assert np.allclose(got, want, rtol=1e-14)
+
+
+def test_moment_product_single_tensor_is_the_moment(orc):
+    shape = (4, 3, 5)
+    p = np.random.default_rng(53).random(60)
+    assert np.allclose(orc.moment_product([p], [shape], "f64"), orc.moment(p, shape, "f64"), rtol=1e-15)
+
+
 # ---------------------------------------------------------------- convolution (Alg 14)
 
 def test_convolution_against_scipy(orc):
