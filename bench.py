@@ -458,8 +458,29 @@ def run_extra_workloads(args, triot, synth, dev, stream):
         r["product"] = op_entry(3 * es * nI, ms, peak, nI)
         ms = time_op(lambda k, st: triot.triot_moment(R[k % ncopy], out=out, workspace=ws, stream=st), 3 * ncopy, stream)
         r["moment"] = op_entry(es * nI, ms, peak, nI)
+        # the same pipeline fused: the moment of p*q over I, without writing r
+        wsp = torch.empty(triot.triot_moment_product_workspace_size([pc.pshape, pc.qshape], dt) // 8 + 2,
+                          dtype=torch.float64, device=dev)
+        ms = time_op(lambda k, st: triot.triot_moment_product([P[k % ncopy], Q[k % ncopy]], out=out,
+                                                              workspace=wsp, stream=st), 3 * ncopy, stream)
+        r["moment_product"] = op_entry(2 * es * nI, ms, peak, nI)
         res[f"precision_{name}"] = r
         del P, Q, R
+    torch.cuda.empty_cache()
+    # moment of the product of the f64 d=8 pair (x 9^8, y (12,8)x4) over I = (9,8)x4, fused:
+    # 2 * 8 * |I| bytes read, against 4 * 8 * |I| for the product followed by the moment
+    c8 = synth.config_f64_d8()
+    I8 = tuple(min(a, b) for a, b in zip(c8.xshape, c8.prod_shape))
+    n8 = int(np.prod(I8))
+    x8 = torch.from_numpy(c8.x_values().reshape(c8.xshape)).to(dev)
+    y8 = torch.from_numpy(c8.yprod_values().reshape(c8.prod_shape)).to(dev)
+    out8 = torch.empty(len(I8) + 1, dtype=torch.float64, device=dev)
+    ws8 = torch.empty(triot.triot_moment_product_workspace_size([c8.xshape, c8.prod_shape], torch.float64) // 8 + 2,
+                      dtype=torch.float64, device=dev)
+    ms = time_op(lambda k, st: triot.triot_moment_product([x8, y8], out=out8, workspace=ws8, stream=st), 20, stream)
+    res["moment_product_f64_d8"] = {"moment_product": op_entry(2 * 8 * n8, ms, peak, n8),
+                                    "unfused_bytes": 4 * 8 * n8, "intersection": list(I8)}
+    del x8, y8
     torch.cuda.empty_cache()
     return res
 
@@ -544,6 +565,23 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_op(args):
+    """A few calls of one op on its workload, for an ncu capture (no JSON line)."""
+    import torch
+    from paper_1608_00099_gb300 import synth, triot
+    dev = torch.device("cuda", 0)
+    c8 = synth.config_f64_d8()
+    x8 = torch.from_numpy(c8.x_values().reshape(c8.xshape)).to(dev)
+    y8 = torch.from_numpy(c8.yprod_values().reshape(c8.prod_shape)).to(dev)
+    out = torch.empty(len(c8.xshape) + 1, dtype=torch.float64, device=dev)
+    ws = torch.empty(triot.triot_moment_product_workspace_size([c8.xshape, c8.prod_shape], torch.float64) // 8 + 2,
+                     dtype=torch.float64, device=dev)
+    for _ in range(max(1, args.steps)):
+        triot.triot_moment_product([x8, y8], out=out, workspace=ws)
+    torch.cuda.synchronize()
+    print(f"{args.profile_op}: {max(1, args.steps)} calls done", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,7 +598,11 @@ def main():
     ap.add_argument("--no-big", action="store_true", help="skip the 44 GB f32 d=24 workload")
     ap.add_argument("--autotune", default="", help="autotune the three ops and save the cache here")
     ap.add_argument("--no-tune-file", action="store_true", help="ignore the committed tuning file")
+    ap.add_argument("--profile-op", default="", choices=["", "moment_product_f64_d8"],
+                    help="only run one op a few times (the command the ncu summaries capture)")
     args = ap.parse_args()
+    if args.profile_op:
+        return profile_op(args)
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local, dist = dist_setup()

@@ -115,10 +115,12 @@ int triot_moment_workspace_size(int rank, const int64_t* shape, int dtype, size_
  *   p: device tensor, read only.  out: DEVICE array of rank+1 doubles, written.
  *   workspace: device scratch of at least triot_moment_workspace_size() bytes, 16-byte
  *   aligned, owned by the caller; its contents on entry are ignored.
- *   Accumulation: f64 input in exact fixed point (one rounding to f64 per block and one
- *   at the end); f32/bf16/f16 input in compensated f32 per thread.  Block partials are
- *   combined by a second kernel in exact fixed point, so results are bit-identical from
- *   run to run.  Two kernels are enqueued on `stream`.
+ *   Accumulation: f64 input in two's-complement fixed point, exact within windows of at
+ *   most 1024 elements per thread and rounded to f64 once per window (error at most
+ *   2^-52 times the window's largest |p| per element); f32/bf16/f16 input in compensated
+ *   f32 per thread.  Block partials are combined by a second kernel in fixed point,
+ *   independent of their order, so results are bit-identical from run to run.  Two
+ *   kernels are enqueued on `stream`.
  */
 int triot_moment(int rank, const int64_t* shape, const void* p, int dtype, double* out,
                  void* workspace, size_t workspace_bytes, void* stream);
@@ -144,6 +146,38 @@ int triot_moment(int rank, const int64_t* shape, const void* p, int dtype, doubl
 #define TRIOT_MOMENT_NOALLOC_MAX_DOUBLES 65536
 int triot_moment_noalloc(int rank, const int64_t* shape, const void* p, int dtype, double* out,
                          void* stream);
+
+/*
+ * triot_moment_product_workspace_size -- bytes of device workspace triot_moment_product
+ *   needs for these shapes and dtype.  Writes *bytes.
+ */
+int triot_moment_product_workspace_size(int rank, int ntensors, const int64_t* const* shapes,
+                                        int dtype, size_t* bytes);
+
+/*
+ * triot_moment_product -- the tuple-weighted moment of a product of tensors over the
+ *   tuples their shapes share (Algorithm 11 weights the tuple by x[t]*y[t]*z[t]; with two
+ *   tensors out[rank] is the inner product over the shared tuples of Section 3's second
+ *   benchmark), without forming the product in memory:
+ *       I         = elementwise minimum of the shapes
+ *       w[t]      = x_0[t] * x_1[t] * ... * x_{n-1}[t], left to right
+ *       out[i]    = sum over tuples t of I  w[t] * t_i     (i = 0 .. rank-1, zero-based)
+ *       out[rank] = sum over tuples t of I  w[t]
+ *   ntensors: 1 .. 4.  shapes[k]: HOST array of rank extents of tensor k; tensors[k]:
+ *   its DEVICE data (dense row-major, read only), all of the same dtype.  The products are
+ *   rounded to nearest even in double for TRIOT_F64 and in float for TRIOT_F32, TRIOT_BF16
+ *   and TRIOT_F16 (whose values float holds exactly).  out: DEVICE array of rank+1 doubles.
+ *   workspace: device scratch of at least triot_moment_product_workspace_size() bytes,
+ *   16-byte aligned.  Sums are fixed point, exact within windows of at most 1024 elements
+ *   per thread (error at most 2^-52 times the window's largest |w| per element for f64
+ *   tensors, 2^-48 for the others); partials are combined independently of their order.
+ *   Errors: TRIOT_ERR_ARG (ntensors outside 1..4), TRIOT_ERR_RANK, TRIOT_ERR_SHAPE
+ *   (negative extent, extent >= 2^31), TRIOT_ERR_NULL, TRIOT_ERR_DTYPE,
+ *   TRIOT_ERR_WORKSPACE, TRIOT_ERR_CUDA.  An empty intersection writes zeros.
+ */
+int triot_moment_product(int rank, int ntensors, const int64_t* const* shapes,
+                         const void* const* tensors, int dtype, double* out, void* workspace,
+                         size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------ batched launch */
 

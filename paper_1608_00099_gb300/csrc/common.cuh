@@ -115,6 +115,32 @@ struct MomentGeom {
   long long ext[kMaxRank];         // extents (axis order, outermost first)
 };
 
+// Moment of a product of tensors over the intersection I of their shapes.  I's unit axes
+// are dropped (their digit is always 0); axis D-1 is the row (inner) axis.
+constexpr int kMProdMaxTensors = 4;
+constexpr int kMProdWarps = 4;           // warps per CTA
+constexpr int kMProdWindow = 1024;       // elements a lane sums in one fixed-point window
+constexpr int kMProdLC = 8;              // row elements a lane loads before using any
+struct MProdGeom {
+  int D;                                 // rank of the canonical I (>= 1)
+  int unit_inner;                        // every tensor has stride 1 on the row axis
+  long long L;                           // row length (extent of axis D-1)
+  long long nrows;                       // rows: product of the extents of axes 0..D-2
+  long long nround;                      // rounds of 32 rows
+  long long ext[kMaxRank];               // extents of I
+  FastDiv div[kMaxRank];                 // the same, for the 32-bit decode
+  int n32;                               // nrows < 2^32
+  uint32_t jd[kMaxRank];                 // digits of a 32-row step, axes 0..D-2 (axis 0 takes
+                                         // the remainder)
+  const void* x[kMProdMaxTensors];       // the tensors
+  long long stride[kMProdMaxTensors][kMaxRank];  // their element strides on I's axes
+};
+__host__ __device__ constexpr int mprod_levels(int DO) { return DO >= 4 ? DO - 3 : 0; }
+__host__ __device__ constexpr int mprod_qlevels(int DO) { return DO >= 5 ? DO - 4 : 0; }
+__host__ __device__ constexpr int mprod_dyn_smem(int DO) {
+  return kMProdWarps * 32 * (mprod_levels(DO) * 20 + mprod_qlevels(DO) * 16 + DO * 8);
+}
+
 struct CombineGeom {
   int D;                           // effective rank
   int rank;                        // caller's rank (output length rank + 1)

@@ -17,4 +17,6 @@ const void* moment_blk64_kernel_ptr(int B, int DO);
 // sticky flag of the f64 block kernel (a bounded wait gave up); reading clears it
 void b64_read_device_flag(int* flag);
 const void* combine_kernel_ptr();
+// moment of a product of tensors: one kernel per dtype and tensor count (1..4)
+const void* moment_prod_kernel_ptr(int dtype, int ntensors);
 }  // namespace triot

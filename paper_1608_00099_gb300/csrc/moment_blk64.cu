@@ -36,42 +36,6 @@
 namespace triot {
 namespace {
 
-// v * 2^k rounded to f64 (nearest, ties to even) with 64-bit integer operations; the FP64
-// pipe of this GPU is narrow, so it is used only where the result leaves the normal range
-__device__ __forceinline__ double fixed_to_double(__int128 v, int k) {
-  if (v == 0) return 0.0;
-  const bool neg = v < 0;
-  const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
-  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-  // t: the top 64 significant bits (leading bit at 63); sticky: any bit below them
-  unsigned long long t;
-  bool sticky;
-  int e;  // exponent of the leading bit
-  if (hi == 0) {
-    const int lz = __clzll((long long)lo);
-    t = lo << lz;
-    sticky = false;
-    e = 63 - lz + k;
-  } else {
-    const int lz = __clzll((long long)hi);
-    t = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
-    sticky = lz ? (lo << lz) != 0 : lo != 0;
-    e = 127 - lz + k;
-  }
-  if (e < -1022 || e > 1023) {
-    const int k1 = k / 2, k2 = k - k1;
-    return i128_to_double(v) * __longlong_as_double((long long)(k1 + 1023) << 52) *
-           __longlong_as_double((long long)(k2 + 1023) << 52);
-  }
-  unsigned long long mant = t >> 11;  // 53 bits
-  const unsigned r = (unsigned)(t & 0x7FFull);
-  if (r > 0x400u || (r == 0x400u && (sticky || (mant & 1ull)))) ++mant;
-  // mant in [2^52, 2^53]; a carry to 2^53 moves into the exponent field by itself
-  const unsigned long long bits =
-      ((unsigned long long)(e + 1022) << 52) + mant + (neg ? 0x8000000000000000ull : 0ull);
-  return __longlong_as_double((long long)bits);
-}
-
 // set when a bounded wait for a bulk copy gives up (read by triot_device_status)
 __device__ int g_b64_flag = 0;
 
@@ -80,43 +44,9 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// acc += a * b exactly (the 128-bit product from the low and high 64-bit halves)
-__device__ __forceinline__ void mac128(__int128& acc, long long a, long long b) {
-  const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
-  const long long hi = __mul64hi(a, b);
-  acc += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
-}
-
-// acc += a * t exactly for |a| < 2^95 (the product stays inside 128 bits)
-__device__ __forceinline__ void mac128x32(__int128& acc, __int128 a, uint32_t t) {
-  const unsigned long long lo = (unsigned long long)a;
-  const long long hi = (long long)(a >> 64);
-  const unsigned long long plo = lo * (unsigned long long)t;
-  const unsigned long long phi = __umul64hi(lo, (unsigned long long)t) + (unsigned long long)(hi * (long long)t);
-  acc += (__int128)(((unsigned __int128)phi << 64) | plo);
-}
-
-// acc += a * t exactly for 0 <= t < 2^31 (two 32x32 -> 64-bit products)
-__device__ __forceinline__ void mac64x32(__int128& acc, long long a, uint32_t t) {
-  const unsigned long long p0 = (unsigned long long)(uint32_t)a * (unsigned long long)t;
-  const long long p1 = (long long)(int)(a >> 32) * (long long)t;
-  acc += (__int128)p0 + ((__int128)p1 << 32);
-}
-
-__device__ __forceinline__ long long shr64(long long v, int d) {
-  return d >= 63 ? (v < 0 ? -1ll : 0ll) : (v >> d);
-}
-
-// one lane's column of a lane-major shared-memory array: element i of this lane
-template <typename T>
-struct LaneCol {
-  T* p;
-  __device__ __forceinline__ T& operator[](int i) const { return p[i * (kB64Warps * 32)]; }
-};
-
 // non-finite element: plain f64 sums of v * t_i (rare; kept out of line)
 __device__ __noinline__ void add_special(double v, uint32_t t1, uint32_t t2, uint32_t t3,
-                                         LaneCol<uint32_t> tc, int DO, int m,
+                                         LaneCol<uint32_t, kB64Warps * 32> tc, int DO, int m,
                                          const unsigned char* dig_j, double* Asp, double* Isp,
                                          double* Psp) {
   if (DO >= 1) Asp[DO - 1] += v * (double)t1;
@@ -273,13 +203,13 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
   // axes 0 .. DO-4 and the lane's f64 totals: lane-major dynamic shared memory after the
   // stages (touched at carries and window ends; run-time axis index)
   unsigned char* st_base = dsm + (size_t)b64_stage_bytes(B);
-  const LaneCol<__int128> Ac{reinterpret_cast<__int128*>(st_base) + threadIdx.x};
+  const LaneCol<__int128, T> Ac{reinterpret_cast<__int128*>(st_base) + threadIdx.x};
   st_base += (size_t)b64_levels(DO) * T * 16;
-  const LaneCol<__int128> Qc{reinterpret_cast<__int128*>(st_base) + threadIdx.x};
+  const LaneCol<__int128, T> Qc{reinterpret_cast<__int128*>(st_base) + threadIdx.x};
   st_base += (size_t)b64_qlevels(DO) * T * 16;
-  const LaneCol<double> Ads{reinterpret_cast<double*>(st_base) + threadIdx.x};
+  const LaneCol<double, T> Ads{reinterpret_cast<double*>(st_base) + threadIdx.x};
   st_base += (size_t)DO * T * 8;
-  const LaneCol<uint32_t> tc{reinterpret_cast<uint32_t*>(st_base) + threadIdx.x};
+  const LaneCol<uint32_t, T> tc{reinterpret_cast<uint32_t*>(st_base) + threadIdx.x};
   for (int i = 0; i < b64_levels(DO); ++i) { Ac[i] = 0; tc[i] = 0; }
   for (int i = 0; i < b64_qlevels(DO); ++i) Qc[i] = 0;
   for (int i = 0; i < DO; ++i) Ads[i] = 0.0;

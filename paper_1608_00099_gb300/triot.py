@@ -67,6 +67,8 @@ def lib() -> C.CDLL:
             "triot_moment_workspace_size": (i, [i, _I64P, i, C.POINTER(sz)]),
             "triot_moment": (i, [i, _I64P, vp, i, vp, vp, sz, vp]),
             "triot_moment_noalloc": (i, [i, _I64P, vp, i, vp, vp]),
+            "triot_moment_product_workspace_size": (i, [i, i, C.POINTER(_I64P), i, C.POINTER(sz)]),
+            "triot_moment_product": (i, [i, i, C.POINTER(_I64P), C.POINTER(vp), i, vp, vp, sz, vp]),
             "triot_batch_plan_create": (i, [C.POINTER(BatchDesc), i, i, i, C.POINTER(Tune), C.POINTER(vp)]),
             "triot_batch_run": (i, [vp, vp]),
             "triot_batch_run_plain": (i, [vp, vp]),
@@ -179,6 +181,43 @@ def triot_moment(p: torch.Tensor, out: torch.Tensor | None = None, workspace: to
         raise TriotError(8, "out must hold rank + 1 float64 values")
     _check(lib().triot_moment(rank, _shape(p.shape), _dev(p), _dtype(p), _dev(out), _dev(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
+    return out
+
+
+def _shape_table(shapes):
+    arrs = [_shape(s) for s in shapes]
+    table = (_I64P * len(arrs))(*[C.cast(a, _I64P) for a in arrs])
+    return table, arrs          # keep the arrays alive with the table
+
+
+def triot_moment_product_workspace_size(shapes, dtype: torch.dtype) -> int:
+    table, _keep = _shape_table(shapes)
+    n = C.c_size_t(0)
+    _check(lib().triot_moment_product_workspace_size(len(shapes[0]), len(shapes), table, DTYPE_CODE[dtype],
+                                                     C.byref(n)))
+    return int(n.value)
+
+
+def triot_moment_product(tensors, out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """Moment of w = x_0 * x_1 * ... over the intersection of the shapes (all tensors of one
+    dtype and rank, on one device): out[i] = sum_t w[t] t_i, out[rank] = sum_t w[t]."""
+    tensors = list(tensors)
+    rank = tensors[0].dim()
+    dev = tensors[0].device
+    if out is None:
+        out = torch.empty(rank + 1, dtype=torch.float64, device=dev)
+    if out.dtype != torch.float64 or out.numel() < rank + 1:
+        raise TriotError(8, "out must hold rank + 1 float64 values")
+    shapes = [tuple(t.shape) for t in tensors]
+    if workspace is None:
+        nb = triot_moment_product_workspace_size(shapes, tensors[0].dtype)
+        workspace = torch.empty((nb + 15) // 16 * 2, dtype=torch.float64, device=dev)
+    table, _keep = _shape_table(shapes)
+    ptrs = (C.c_void_p * len(tensors))(*[_dev(t) for t in tensors])
+    _check(lib().triot_moment_product(rank, len(tensors), table, ptrs, _dtype(tensors[0]), _dev(out),
+                                      _dev(workspace), workspace.numel() * workspace.element_size(),
+                                      _stream(stream)))
     return out
 
 

@@ -129,6 +129,18 @@ def test_bad_arguments_fail_before_any_gpu_work(tr):
     assert L.triot_product(3, s3, fake, s3, None, 1, None) == 3
     assert L.triot_moment(3, tr._shape((2, 2 ** 31, 1)), fake, 0, fake2, fake2, 1 << 20, None) == 2
     assert "must be < 2^31" in L.triot_last_error().decode()
+    # the moment of a product: tensor count, extents and pointers are checked first
+    shp = (tr._I64P * 2)(C.cast(s3, tr._I64P), C.cast(big, tr._I64P))
+    ptrs = (C.c_void_p * 2)(fake, fake2)
+    assert L.triot_moment_product(3, 0, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 8      # no tensors
+    assert L.triot_moment_product(3, 5, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 8      # five
+    assert L.triot_moment_product(0, 2, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 1      # rank 0
+    assert L.triot_moment_product(3, 2, shp, ptrs, 9, fake2, fake2, 1 << 20, None) == 4      # dtype
+    assert L.triot_moment_product(3, 2, None, ptrs, 0, fake2, fake2, 1 << 20, None) == 3     # NULL shapes
+    neg = (tr._I64P * 2)(C.cast(s3, tr._I64P), C.cast(tr._shape((2, -1, 4)), tr._I64P))
+    assert L.triot_moment_product(3, 2, neg, ptrs, 0, fake2, fake2, 1 << 20, None) == 2
+    nbytes = C.c_size_t(0)
+    assert L.triot_moment_product_workspace_size(3, 0, shp, 0, C.byref(nbytes)) == 8
     # empty iterations are no-ops and succeed without touching the device
     assert L.triot_product(2, tr._shape((0, 3)), None, tr._shape((2, 3)), None, 0, None) == 0
     assert L.triot_crop(2, tr._shape((2, 0)), None, tr._shape((2, 3)), None, 0, None) == 0
