@@ -467,6 +467,19 @@ def run_extra_workloads(args, triot, synth, dev, stream):
         res[f"precision_{name}"] = r
         del P, Q, R
     torch.cuda.empty_cache()
+    # views (Section 4's biased slices): the FFT-style centre pad of x (8)^6 into y (16)^6 at
+    # (4)^6 and the extraction back; y (134 MB) is larger than L2
+    xs6, ys6, st6 = (8,) * 6, (16,) * 6, (4,) * 6
+    xv = torch.from_numpy(synth.normal01(1006, 8 ** 6).reshape(xs6)).to(dev)
+    yv = [torch.empty(ys6, dtype=torch.float64, device=dev) for _ in range(2)]
+    ms = time_op(lambda k, st: triot.triot_embed_at(xv, yv[k % 2], st6, stream=st), 6, stream)
+    r = {"embed_at": op_entry(8 * (8 ** 6 + 16 ** 6), ms, peak, 16 ** 6)}
+    xb = [torch.empty(xs6, dtype=torch.float64, device=dev) for _ in range(2)]
+    ms = time_op(lambda k, st: triot.triot_crop_at(xb[k % 2], yv[k % 2], st6, stream=st), 6, stream)
+    r["crop_at"] = op_entry(2 * 8 * 8 ** 6, ms, peak, 8 ** 6)
+    res["fft_pad_f64_d6"] = r
+    del xv, yv, xb
+    torch.cuda.empty_cache()
     # moment of the product of the f64 d=8 pair (x 9^8, y (12,8)x4) over I = (9,8)x4, fused:
     # 2 * 8 * |I| bytes read, against 4 * 8 * |I| for the product followed by the moment
     c8 = synth.config_f64_d8()

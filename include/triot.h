@@ -101,6 +101,30 @@ int triot_product(int rank, const int64_t* xshape, const void* x, const int64_t*
                   void* y, int dtype, void* stream);
 
 /*
+ * Views (Section 4: a slice references its tensor and adds a bias -- the flat index of its
+ * start tuple computed with the tensor's own shape -- to every flat index).  `ystart` is a
+ * HOST array of rank non-negative starts; the window of y is the tuples ystart + t.
+ *
+ * triot_embed_at  -- y[ystart + t] = x[t] for every tuple t of x's shape; every other element
+ *   of y is set to +0 unless flags has TRIOT_EMBED_NOPAD (then it is left untouched).
+ *   Requires ystart + xshape <= yshape on every axis (TRIOT_ERR_SHAPE otherwise).  Without
+ *   NOPAD two kernels are enqueued (the pad over all of y, then the copy).
+ * triot_crop_at   -- x[t] = y[ystart + t] for every tuple t of x's shape (the inverse: the
+ *   extraction step after a zero-padded transform).  Same requirement.
+ * triot_product_at -- y[ystart + t] *= x[t] for every tuple t of x's shape with
+ *   ystart + t inside y (the intersection of x's shape with y's remainder yshape - ystart);
+ *   requires ystart <= yshape.  Rounding as triot_product.
+ * Other arguments, errors and aliasing rules as the whole-tensor calls (x and y must not
+ * overlap anywhere in their containers).
+ */
+int triot_embed_at(int rank, const int64_t* xshape, const void* x, const int64_t* yshape, void* y,
+                   const int64_t* ystart, int dtype, unsigned flags, void* stream);
+int triot_crop_at(int rank, const int64_t* xshape, void* x, const int64_t* yshape, const void* y,
+                  const int64_t* ystart, int dtype, void* stream);
+int triot_product_at(int rank, const int64_t* xshape, const void* x, const int64_t* yshape, void* y,
+                     const int64_t* ystart, int dtype, void* stream);
+
+/*
  * triot_moment_workspace_size -- bytes of device workspace triot_moment needs for this
  *   shape and dtype (per-block partial sums).  Writes *bytes; never fails for valid
  *   arguments.  The size depends only on (rank, shape, dtype) and the tuning in force.

@@ -48,6 +48,9 @@ def load(path: str):
     L.oracle_product_window.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p,
                                         C.c_uint64, C.c_uint64, C.c_void_p]
     L.oracle_moment.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, C.POINTER(C.c_double), C.c_int]
+    L.oracle_embed_at.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, _u64p, C.c_int]
+    L.oracle_crop_at.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, _u64p]
+    L.oracle_product_at.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, _u64p]
     L.oracle_moment_product.argtypes = [C.c_int, C.c_uint, C.c_uint, _u64p, C.POINTER(C.c_void_p),
                                         C.POINTER(C.c_double)]
     L.oracle_convolve_f64.argtypes = [C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, C.c_void_p]
@@ -203,6 +206,38 @@ def moment(p: np.ndarray, shape, dtype: str, nthreads: int = 1) -> np.ndarray:
     lib().oracle_moment(DTYPES[dtype], len(s), _p(s), _buf(p),
                         out.ctypes.data_as(C.POINTER(C.c_double)), nthreads)
     return out
+
+
+def embed_at(x: np.ndarray, xshape, yshape, ystart, dtype: str, y: np.ndarray | None = None) -> np.ndarray:
+    """y[ystart + t] = x[t] over x's shape; the rest of y is +0 (or, given y, left as is)."""
+    xs, ys, st = _shape(xshape), _shape(yshape), _shape(ystart)
+    x = np.ascontiguousarray(x).reshape(-1)
+    _check(x, dtype, int(np.prod(xs)))
+    pad = y is None
+    y = np.empty(int(np.prod(ys)), dtype=NP_STORAGE[dtype]) if pad else np.ascontiguousarray(y).reshape(-1).copy()
+    lib().oracle_embed_at(DTYPES[dtype], len(xs), _p(xs), _buf(x), _p(ys), _buf(y), _p(st), int(pad))
+    return y
+
+
+def crop_at(y: np.ndarray, xshape, yshape, ystart, dtype: str) -> np.ndarray:
+    """x[t] = y[ystart + t] over x's shape."""
+    xs, ys, st = _shape(xshape), _shape(yshape), _shape(ystart)
+    y = np.ascontiguousarray(y).reshape(-1)
+    _check(y, dtype, int(np.prod(ys)))
+    x = np.empty(int(np.prod(xs)), dtype=NP_STORAGE[dtype])
+    lib().oracle_crop_at(DTYPES[dtype], len(xs), _p(xs), _buf(x), _p(ys), _buf(y), _p(st))
+    return x
+
+
+def product_at(x: np.ndarray, xshape, y: np.ndarray, yshape, ystart, dtype: str) -> np.ndarray:
+    """A copy of y with y[ystart + t] *= x[t] over the tuples of x that fit in y."""
+    xs, ys, st = _shape(xshape), _shape(yshape), _shape(ystart)
+    x = np.ascontiguousarray(x).reshape(-1)
+    y = np.ascontiguousarray(y).reshape(-1).copy()
+    _check(x, dtype, int(np.prod(xs)))
+    _check(y, dtype, int(np.prod(ys)))
+    lib().oracle_product_at(DTYPES[dtype], len(xs), _p(xs), _buf(x), _p(ys), _buf(y), _p(st))
+    return y
 
 
 def moment_product(tensors, shapes, dtype: str) -> np.ndarray:

@@ -461,6 +461,57 @@ void oracle_moment(int dtype, unsigned dim, const u64* shape, const void* p, dou
 
 // ------------------------------------------------------------------ convolution
 
+// Views of y starting at the tuple `ystart` (Section 4: the slice's flat index is the
+// tensor's flat index of the start tuple -- its bias -- plus the flat index of the tuple
+// within the slice, both by Horner's rule on y's own shape).  The tuples t walk x's shape
+// (embed, crop) or the part of it that fits in y (product) with Algorithm 3.
+void oracle_embed_at(int dtype, unsigned dim, const u64* xshape, const void* x, const u64* yshape,
+                     void* y, const u64* ystart, int pad) {
+  const size_t es = elem_size(dtype);
+  if (pad) std::memset(y, 0, size_t(count_of(yshape, dim)) * es);
+  const u64 n = count_of(xshape, dim);
+  if (n == 0) return;
+  const u64 bias = tuple_to_index(ystart, yshape, dim);
+  std::vector<u64> t(dim, 0);
+  for (u64 k = 0; k < n; ++k) {
+    std::memcpy(static_cast<char*>(y) + (bias + tuple_to_index(t.data(), yshape, dim)) * es,
+                static_cast<const char*>(x) + k * es, es);
+    advance_tuple(t.data(), xshape, dim);
+  }
+}
+
+void oracle_crop_at(int dtype, unsigned dim, const u64* xshape, void* x, const u64* yshape,
+                    const void* y, const u64* ystart) {
+  const size_t es = elem_size(dtype);
+  const u64 n = count_of(xshape, dim);
+  if (n == 0) return;
+  const u64 bias = tuple_to_index(ystart, yshape, dim);
+  std::vector<u64> t(dim, 0);
+  for (u64 k = 0; k < n; ++k) {
+    std::memcpy(static_cast<char*>(x) + k * es,
+                static_cast<const char*>(y) + (bias + tuple_to_index(t.data(), yshape, dim)) * es, es);
+    advance_tuple(t.data(), xshape, dim);
+  }
+}
+
+void oracle_product_at(int dtype, unsigned dim, const u64* xshape, const void* x, const u64* yshape,
+                       void* y, const u64* ystart) {
+  std::vector<u64> I(dim);
+  for (unsigned i = 0; i < dim; ++i) {
+    const u64 room = yshape[i] - ystart[i];
+    I[i] = xshape[i] < room ? xshape[i] : room;
+  }
+  const u64 n = count_of(I.data(), dim);
+  if (n == 0) return;
+  const u64 bias = tuple_to_index(ystart, yshape, dim);
+  std::vector<u64> t(dim, 0);
+  for (u64 k = 0; k < n; ++k) {
+    multiply_into(y, bias + tuple_to_index(t.data(), yshape, dim), x,
+                  tuple_to_index(t.data(), xshape, dim), dtype);
+    advance_tuple(t.data(), I.data(), dim);
+  }
+}
+
 // The moment of a product of tensors over the intersection I of their shapes (Algorithm
 // 11 weights the tuple by x[t]*y[t]*z[t]; with two tensors the mass is benchmark 2's inner
 // product over the tuples both shapes share, Section 3):

@@ -68,13 +68,13 @@ static int64_t count(int rank, const int64_t* s) {
 // ------------------------------------------------------------------ row ops
 int launch_rows(int op, int rank, const int64_t* xshape, const void* x, const int64_t* yshape,
                 const void* y, int dtype, unsigned flags, cudaStream_t stream,
-                const TuneCfg* force) {
+                const TuneCfg* force, const int64_t* xdata, const int64_t* ydata) {
   if (!valid_dtype(dtype)) return fail(TRIOT_ERR_DTYPE, "unknown dtype code");
   if (op == ROW_EMBED && (flags & ~TRIOT_EMBED_NOPAD)) return fail(TRIOT_ERR_ARG, "unknown embed flag");
   Canon c;
   bool x_empty = false;
   std::string err;
-  int st = canon_rows(op, rank, xshape, yshape, c, x_empty, err);
+  int st = canon_rows(op, rank, xshape, yshape, c, x_empty, err, xdata, ydata);
   if (st) return fail(st, err);
   const int es = dtype_size(dtype);
   const int64_t nx = count(rank, xshape), ny = count(rank, yshape);
@@ -83,7 +83,8 @@ int launch_rows(int op, int rank, const int64_t* xshape, const void* x, const in
   if (!work) return ok();
   if ((op != ROW_EMBED || nx > 0) && !x) return fail(TRIOT_ERR_NULL, "x is NULL");
   if (!y) return fail(TRIOT_ERR_NULL, "y is NULL");
-  if (x && nx > 0 && overlaps_bytes(x, size_t(nx) * es, y, size_t(ny) * es))
+  // (views: the caller checks the whole containers)
+  if (!xdata && !ydata && x && nx > 0 && overlaps_bytes(x, size_t(nx) * es, y, size_t(ny) * es))
     return fail(TRIOT_ERR_ALIAS, "x and y overlap");
   DeviceInfo dev;
   if ((st = device_info(dev))) return st;

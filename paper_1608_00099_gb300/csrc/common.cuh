@@ -90,6 +90,8 @@ struct RowGeom {
   FastDiv seg_div;                 // divisor = segs_per_row
   int rows32;                      // rows fit the 32-bit decode
   int nopad;                       // embed: skip writing the pad
+  int a_dense;                     // A's rows lie back to back (offset = row * inner); 0 for
+                                   // a view of a larger tensor (offsets from the strides)
 };
 
 enum {

@@ -19,8 +19,11 @@ bool valid_dtype(int dt);
 bool overlaps_bytes(const void* a, size_t na, const void* b, size_t nb);
 
 // row ops with an explicit geometry (force != nullptr) or the cached one
+// xdata / ydata: container shapes when x / y are views (their pointers already carry the
+// view's bias); nullptr for whole tensors
 int launch_rows(int op, int rank, const int64_t* xshape, const void* x, const int64_t* yshape,
-                const void* y, int dtype, unsigned flags, cudaStream_t stream, const TuneCfg* force);
+                const void* y, int dtype, unsigned flags, cudaStream_t stream, const TuneCfg* force,
+                const int64_t* xdata = nullptr, const int64_t* ydata = nullptr);
 
 // moment: plan, workspace bytes, launch
 int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, const TuneCfg* force,

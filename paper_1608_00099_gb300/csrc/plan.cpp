@@ -31,7 +31,7 @@ long long gcd_ll(long long a, long long b) {
 }  // namespace
 
 int canon_rows(int op, int rank, const int64_t* xshape, const int64_t* yshape, Canon& c,
-               bool& x_empty, std::string& err) {
+               bool& x_empty, std::string& err, const int64_t* xdata, const int64_t* ydata) {
   char buf[256];
   if (rank < 1 || rank > kMaxRank) {
     snprintf(buf, sizeof buf, "rank %d outside [1, %d]", rank, kMaxRank);
@@ -60,8 +60,9 @@ int canon_rows(int op, int rank, const int64_t* xshape, const int64_t* yshape, C
     ny *= yshape[i];
   }
   int64_t ext[kMaxRank], sx[kMaxRank], sy[kMaxRank], sa[kMaxRank], sb[kMaxRank], bound[kMaxRank];
-  strides_of(rank, xshape, sx);
-  strides_of(rank, yshape, sy);
+  // strides from the containers' shapes (a view addresses its container, Section 4)
+  strides_of(rank, xdata ? xdata : xshape, sx);
+  strides_of(rank, ydata ? ydata : yshape, sy);
   x_empty = (nx == 0);
   for (int i = 0; i < rank; ++i) {
     if (op == ROW_EMBED) { ext[i] = yshape[i]; sa[i] = sy[i]; sb[i] = sx[i]; bound[i] = xshape[i]; }
@@ -191,12 +192,21 @@ void plan_rows(int op, const Canon& c, bool x_empty, int es, const void* A, cons
   for (int k = 0; k < g.nouter; ++k)
     g.div[k] = make_fastdiv(g.ext[k] < 0xFFFFFFFFll ? (uint32_t)g.ext[k] : 1u);
   g.nopad = (op == ROW_EMBED && (flags & TRIOT_EMBED_NOPAD)) ? 1 : 0;
+  {
+    long long expect = g.inner;
+    g.a_dense = 1;
+    for (int k = 0; k < g.nouter; ++k) {
+      if (g.sa[k] != expect) g.a_dense = 0;
+      expect *= g.ext[k];
+    }
+  }
 
   const bool a_al = (reinterpret_cast<uintptr_t>(A) % 16) == 0;
   const bool b_al = (reinterpret_cast<uintptr_t>(B) % 16) == 0;
+  // vector accesses to A need every row of A 16-byte aligned: A's start and all its row
+  // strides (automatic for a dense A whose rows are whole vectors; a view's rows may not be)
   bool row_ok = (g.inner % vec == 0) && a_al;
-  if (op == ROW_PRODUCT)
-    for (int k = 0; k < g.nouter; ++k) row_ok = row_ok && (g.sa[k] % vec == 0);
+  for (int k = 0; k < g.nouter; ++k) row_ok = row_ok && (g.sa[k] % vec == 0);
   bool vec_ok = row_ok && b_al;
   for (int k = 0; k < g.nouter; ++k) vec_ok = vec_ok && (g.sb[k] % vec == 0);
   if (op == ROW_EMBED) vec_ok = vec_ok && (g.b_inner % vec == 0);

@@ -24,8 +24,11 @@ struct DeviceInfo {
 
 // Validate and canonicalise a row operation (ROW_EMBED / ROW_CROP / ROW_PRODUCT).
 // Returns a triot_status code; on error `err` says why.
+// xdata / ydata: shapes of the containers the operands are views of (strides come from
+// them; nullptr: the operand is its own container).
 int canon_rows(int op, int rank, const int64_t* xshape, const int64_t* yshape, Canon& c,
-               bool& x_empty, std::string& err);
+               bool& x_empty, std::string& err, const int64_t* xdata = nullptr,
+               const int64_t* ydata = nullptr);
 // Validate and canonicalise a moment (drop extent-1 axes, keep the axis map).
 int canon_moment(int rank, const int64_t* shape, Canon& c, std::string& err);
 

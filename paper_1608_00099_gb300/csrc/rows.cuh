@@ -80,7 +80,7 @@ __device__ __forceinline__ RowInfo decode_row(const RowGeom& g, long long r) {
       } else {
         t = rem;
       }
-      if (OP == ROW_PRODUCT) oa += (long long)t * g.sa[k];
+      if (OP == ROW_PRODUCT || !g.a_dense) oa += (long long)t * g.sa[k];
       ob += (long long)t * g.sb[k];
       if (OP == ROW_EMBED) inside = inside && ((long long)t < g.bound[k]);
     }
@@ -96,13 +96,13 @@ __device__ __forceinline__ RowInfo decode_row(const RowGeom& g, long long r) {
       } else {
         t = rem;
       }
-      if (OP == ROW_PRODUCT) oa += t * g.sa[k];
+      if (OP == ROW_PRODUCT || !g.a_dense) oa += t * g.sa[k];
       ob += t * g.sb[k];
       if (OP == ROW_EMBED) inside = inside && (t < g.bound[k]);
     }
   }
   RowInfo ri;
-  ri.a = (OP == ROW_PRODUCT) ? oa : r * g.inner;
+  ri.a = (OP == ROW_PRODUCT || !g.a_dense) ? oa : r * g.inner;
   ri.b = (OP == ROW_EMBED && !inside) ? -1 : ob;
   return ri;
 }

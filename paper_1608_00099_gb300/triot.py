@@ -67,6 +67,9 @@ def lib() -> C.CDLL:
             "triot_moment_workspace_size": (i, [i, _I64P, i, C.POINTER(sz)]),
             "triot_moment": (i, [i, _I64P, vp, i, vp, vp, sz, vp]),
             "triot_moment_noalloc": (i, [i, _I64P, vp, i, vp, vp]),
+            "triot_embed_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, u, vp]),
+            "triot_crop_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
+            "triot_product_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
             "triot_moment_product_workspace_size": (i, [i, i, C.POINTER(_I64P), i, C.POINTER(sz)]),
             "triot_moment_product": (i, [i, i, C.POINTER(_I64P), C.POINTER(vp), i, vp, vp, sz, vp]),
             "triot_batch_plan_create": (i, [C.POINTER(BatchDesc), i, i, i, C.POINTER(Tune), C.POINTER(vp)]),
@@ -182,6 +185,27 @@ def triot_moment(p: torch.Tensor, out: torch.Tensor | None = None, workspace: to
     _check(lib().triot_moment(rank, _shape(p.shape), _dev(p), _dtype(p), _dev(out), _dev(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
     return out
+
+
+def triot_embed_at(x: torch.Tensor, y: torch.Tensor, ystart, flags: int = 0, stream=None) -> torch.Tensor:
+    """y[ystart + t] = x[t] over x's shape; the rest of y is +0 unless flags has EMBED_NOPAD."""
+    _check(lib().triot_embed_at(x.dim(), _shape(x.shape), _dev(x), _shape(y.shape), _dev(y), _shape(ystart),
+                                _dtype(x), flags, _stream(stream)))
+    return y
+
+
+def triot_crop_at(x: torch.Tensor, y: torch.Tensor, ystart, stream=None) -> torch.Tensor:
+    """x[t] = y[ystart + t] over x's shape."""
+    _check(lib().triot_crop_at(x.dim(), _shape(x.shape), _dev(x), _shape(y.shape), _dev(y), _shape(ystart),
+                               _dtype(x), _stream(stream)))
+    return x
+
+
+def triot_product_at(x: torch.Tensor, y: torch.Tensor, ystart, stream=None) -> torch.Tensor:
+    """y[ystart + t] *= x[t] over the tuples of x that fit in y."""
+    _check(lib().triot_product_at(x.dim(), _shape(x.shape), _dev(x), _shape(y.shape), _dev(y), _shape(ystart),
+                                  _dtype(x), _stream(stream)))
+    return y
 
 
 def _shape_table(shapes):

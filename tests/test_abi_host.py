@@ -141,6 +141,14 @@ def test_bad_arguments_fail_before_any_gpu_work(tr):
     assert L.triot_moment_product(3, 2, neg, ptrs, 0, fake2, fake2, 1 << 20, None) == 2
     nbytes = C.c_size_t(0)
     assert L.triot_moment_product_workspace_size(3, 0, shp, 0, C.byref(nbytes)) == 8
+    # views: the window must fit (embed/crop) or start inside y (product)
+    st = tr._shape((1, 1, 1))
+    assert L.triot_crop_at(3, s3, fake, s3, fake2, st, 0, None) == 2            # 1 + 3 > 3
+    assert L.triot_embed_at(3, s3, fake, big, fake2, tr._shape((0, 0, 1)), 0, 0, None) == 2
+    assert L.triot_product_at(3, s3, fake, s3, fake2, tr._shape((0, 4, 0)), 0, None) == 2   # start > extent
+    assert L.triot_crop_at(3, s3, fake, big, fake2, tr._shape((0, -1, 0)), 0, None) == 2
+    assert L.triot_crop_at(3, s3, fake, big, fake2, None, 0, None) == 3
+    assert L.triot_embed_at(3, s3, fake, big, fake2, tr._shape((1, 0, 0)), 0, 8, None) == 8  # flag
     # empty iterations are no-ops and succeed without touching the device
     assert L.triot_product(2, tr._shape((0, 3)), None, tr._shape((2, 3)), None, 0, None) == 0
     assert L.triot_crop(2, tr._shape((2, 0)), None, tr._shape((2, 3)), None, 0, None) == 0

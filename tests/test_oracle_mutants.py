@@ -41,6 +41,9 @@ MUTANTS = [
     ("product moment addresses every tensor with the first shape",
      "tuple_to_index(t.data(), shapes + k * dim, dim)", "tuple_to_index(t.data(), shapes, dim)",
      [lambda o: pins.test_moment_product_brute_force_f64(o, 0)]),
+    ("view bias computed with x's shape", "const u64 bias = tuple_to_index(ystart, yshape, dim);",
+     "const u64 bias = tuple_to_index(ystart, xshape, dim);",
+     [lambda o: pins.test_views_against_numpy_slicing(o, "f64", 1)]),
     ("bf16 product rounds with f16 parameters",
      "yy[iy] = uint16_t(round_to_format(exact, 8, -126, 127, 8));",
      "yy[iy] = uint16_t(round_to_format(exact, 11, -14, 15, 5));",

@@ -398,6 +398,57 @@ def test_moment_nonfinite_is_the_plain_ieee_sum(orc, nthreads):
             assert (np.isnan(g_) and np.isnan(w_)) or g_ == w_, (bad, got)
 
 
+# ---------------------------------------------------------------- views (Section 4 bias)
+
+VIEW_CASES = [((2, 3), (5, 7), (1, 4)), ((3, 1, 4), (6, 2, 9), (2, 1, 5)), ((4,), (4,), (0,)),
+              ((2, 2, 2, 2), (3, 5, 2, 4), (1, 3, 0, 2)), ((0, 3), (4, 5), (2, 1))]
+
+
+def _slices(st, xs):
+    return tuple(slice(a, a + b) for a, b in zip(st, xs))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", range(len(VIEW_CASES)))
+def test_views_against_numpy_slicing(orc, dtype, case):
+    xs, ys, st = VIEW_CASES[case]
+    rng = np.random.default_rng(80 + case)
+    x = orc.from_f64(rng.standard_normal(int(np.prod(xs))), dtype) if dtype != "f64" else rng.standard_normal(int(np.prod(xs)))
+    y0 = orc.from_f64(rng.standard_normal(int(np.prod(ys))), dtype) if dtype != "f64" else rng.standard_normal(int(np.prod(ys)))
+    # embed at: the window holds x, every other element is +0 (all bits zero)
+    want = np.zeros(ys, dtype=x.dtype)
+    want[_slices(st, xs)] = x.reshape(xs)
+    assert orc.embed_at(x, xs, ys, st, dtype).tobytes() == want.tobytes()
+    # NOPAD: the rest of y keeps its values
+    want2 = y0.reshape(ys).copy()
+    want2[_slices(st, xs)] = x.reshape(xs)
+    assert orc.embed_at(x, xs, ys, st, dtype, y=y0).tobytes() == want2.tobytes()
+    # crop at is the window read back; crop_at(embed_at(x)) = x
+    assert orc.crop_at(y0, xs, ys, st, dtype).tobytes() == np.ascontiguousarray(y0.reshape(ys)[_slices(st, xs)]).tobytes()
+    assert orc.crop_at(orc.embed_at(x, xs, ys, st, dtype), xs, ys, st, dtype).tobytes() == x.tobytes()
+
+
+def test_product_at_against_numpy(orc):
+    xs, ys, st = (4, 6, 3), (5, 8, 4), (2, 3, 2)     # x overhangs y on every axis
+    rng = np.random.default_rng(90)
+    x, y = rng.standard_normal(int(np.prod(xs))), rng.standard_normal(int(np.prod(ys)))
+    got = orc.product_at(x, xs, y, ys, st, "f64").reshape(ys)
+    fit = tuple(min(a, b - s) for a, b, s in zip(xs, ys, st))
+    want = y.reshape(ys).copy()
+    want[_slices(st, fit)] *= x.reshape(xs)[tuple(slice(0, f) for f in fit)]
+    assert got.tobytes() == want.tobytes()
+
+
+def test_bias_is_linear_in_the_tuple(orc):
+    """Section 4's slice rule: idx(start + t) = idx(start) + idx(t) for in-bounds tuples."""
+    shape = (4, 3, 5, 2)
+    for start in [(0, 0, 0, 0), (1, 2, 3, 1), (3, 0, 4, 1)]:
+        room = [s - a for s, a in zip(shape, start)]
+        for t in itertools.product(*[range(r) for r in room]):
+            s_t = [a + b for a, b in zip(start, t)]
+            assert orc.tuple_to_index(s_t, shape) == orc.tuple_to_index(list(start), shape) + orc.tuple_to_index(list(t), shape)
+
+
 # ---------------------------------------------------------------- moment of a product (Alg 11, n-ary)
 
 MP_CASES = [
