@@ -467,6 +467,25 @@ def run_extra_workloads(args, triot, synth, dev, stream):
         res[f"precision_{name}"] = r
         del P, Q, R
     torch.cuda.empty_cache()
+    # benchmark 3 of Section 3 on the paper's shapes, f64: x <- x + y x - z over x's shape;
+    # 4 * 8 * |x| bytes per call, copies rotated so the touched data exceeds 4x L2
+    bx = (2 ** 7 + 1, 2 ** 5, 2 ** 3 + 5, 2 ** 4)
+    by = (2 ** 8 - 3, 2 ** 6, 2 ** 6, 2 ** 4 + 7)
+    bz = (2 ** 8, 2 ** 5 + 7, 2 ** 6, 2 ** 5 + 1)
+    nbx = int(np.prod(bx))
+    per = 4 * 8 * nbx
+    ncopy = int(4 * l2 // per) + 1
+    X0 = torch.from_numpy(synth.normal01(1007, nbx).reshape(bx)).to(dev)
+    Y0 = torch.from_numpy(synth.normal01(1008, int(np.prod(by))).reshape(by)).to(dev)
+    Z0 = torch.from_numpy(synth.normal01(1009, int(np.prod(bz))).reshape(bz)).to(dev)
+    XS = [X0.clone() for _ in range(ncopy)]
+    YS = [Y0.clone() for _ in range(ncopy)]
+    ZS = [Z0.clone() for _ in range(ncopy)]
+    ms = time_op(lambda k, st: triot.triot_apply_xpyxmz(XS[k % ncopy], YS[k % ncopy], ZS[k % ncopy], stream=st),
+                 2 * ncopy, stream)
+    res["apply_benchmark3_f64"] = {"apply_xpyxmz": op_entry(per, ms, peak, nbx), "copies_rotated": ncopy}
+    del X0, Y0, Z0, XS, YS, ZS
+    torch.cuda.empty_cache()
     # views (Section 4's biased slices): the FFT-style centre pad of x (8)^6 into y (16)^6 at
     # (4)^6 and the extraction back; y (134 MB) is larger than L2
     xs6, ys6, st6 = (8,) * 6, (16,) * 6, (4,) * 6

@@ -101,6 +101,21 @@ int triot_product(int rank, const int64_t* xshape, const void* x, const int64_t*
                   void* y, int dtype, void* stream);
 
 /*
+ * triot_apply -- an elementwise operation over three tensors of different shapes, visiting
+ *   every tuple t of x's shape (Algorithm 9's apply with several tensors).  The fixed set of
+ *   operations:
+ *     TRIOT_APPLY_XPYXMZ   x[t] <- x[t] + y[t] * x[t] - z[t]   (Section 3, benchmark 3)
+ *   y and z must contain x's shape on every axis (TRIOT_ERR_SHAPE otherwise); each tensor is
+ *   addressed with its own shape.  Evaluated left to right, each operation rounded to nearest
+ *   even (no fused multiply-add): in double for TRIOT_F64, in float for TRIOT_F32, and in
+ *   float for TRIOT_BF16 / TRIOT_F16 with one final rounding to the storage format.
+ *   x is read and written in place; y and z are read; none may overlap another.
+ */
+#define TRIOT_APPLY_XPYXMZ 1
+int triot_apply(int op, int rank, const int64_t* xshape, void* x, const int64_t* yshape,
+                const void* y, const int64_t* zshape, const void* z, int dtype, void* stream);
+
+/*
  * Views (Section 4: a slice references its tensor and adds a bias -- the flat index of its
  * start tuple computed with the tensor's own shape -- to every flat index).  `ystart` is a
  * HOST array of rank non-negative starts; the window of y is the tuples ystart + t.

@@ -48,6 +48,8 @@ def load(path: str):
     L.oracle_product_window.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p,
                                         C.c_uint64, C.c_uint64, C.c_void_p]
     L.oracle_moment.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, C.POINTER(C.c_double), C.c_int]
+    L.oracle_apply_xpyxmz.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, _u64p,
+                                      C.c_void_p]
     L.oracle_embed_at.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, _u64p, C.c_int]
     L.oracle_crop_at.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, _u64p]
     L.oracle_product_at.argtypes = [C.c_int, C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, _u64p]
@@ -206,6 +208,19 @@ def moment(p: np.ndarray, shape, dtype: str, nthreads: int = 1) -> np.ndarray:
     lib().oracle_moment(DTYPES[dtype], len(s), _p(s), _buf(p),
                         out.ctypes.data_as(C.POINTER(C.c_double)), nthreads)
     return out
+
+
+def apply_xpyxmz(x: np.ndarray, xshape, y: np.ndarray, yshape, z: np.ndarray, zshape, dtype: str) -> np.ndarray:
+    """Benchmark 3: a copy of x with x[t] <- x[t] + y[t] x[t] - z[t] over x's shape."""
+    xs, ys, zs = _shape(xshape), _shape(yshape), _shape(zshape)
+    x = np.ascontiguousarray(x).reshape(-1).copy()
+    y = np.ascontiguousarray(y).reshape(-1)
+    z = np.ascontiguousarray(z).reshape(-1)
+    _check(x, dtype, int(np.prod(xs)))
+    _check(y, dtype, int(np.prod(ys)))
+    _check(z, dtype, int(np.prod(zs)))
+    lib().oracle_apply_xpyxmz(DTYPES[dtype], len(xs), _p(xs), _buf(x), _p(ys), _buf(y), _p(zs), _buf(z))
+    return x
 
 
 def embed_at(x: np.ndarray, xshape, yshape, ystart, dtype: str, y: np.ndarray | None = None) -> np.ndarray:

@@ -461,6 +461,38 @@ void oracle_moment(int dtype, unsigned dim, const u64* shape, const void* p, dou
 
 // ------------------------------------------------------------------ convolution
 
+// Section 3, benchmark 3: x[t] <- x[t] + y[t] * x[t] - z[t] for every tuple t of x's shape,
+// each tensor addressed with its own shape (Algorithm 2; y and z contain x's shape).  The
+// expression is evaluated left to right, ((y*x) then x + that, then minus z), each
+// operation rounded to nearest even: in double for f64, in float for f32, and in float for
+// bf16 / f16 with one final rounding to the storage format.
+void oracle_apply_xpyxmz(int dtype, unsigned dim, const u64* xshape, void* x, const u64* yshape,
+                         const void* y, const u64* zshape, const void* z) {
+  const u64 n = count_of(xshape, dim);
+  if (n == 0) return;
+  std::vector<u64> t(dim, 0);
+  for (u64 k = 0; k < n; ++k) {
+    const u64 iy = tuple_to_index(t.data(), yshape, dim), iz = tuple_to_index(t.data(), zshape, dim);
+    if (dtype == T_F64) {
+      double* xx = static_cast<double*>(x);
+      const double yv = static_cast<const double*>(y)[iy], zv = static_cast<const double*>(z)[iz];
+      const double p = yv * xx[k];
+      const double s = xx[k] + p;
+      xx[k] = s - zv;
+    } else {
+      const float xv = float(load_as_double(x, k, dtype)), yv = float(load_as_double(y, iy, dtype)),
+                  zv = float(load_as_double(z, iz, dtype));
+      const float p = yv * xv;
+      const float s = xv + p;
+      const float r = s - zv;
+      if (dtype == T_F32) static_cast<float*>(x)[k] = r;
+      else if (dtype == T_BF16) static_cast<uint16_t*>(x)[k] = uint16_t(round_to_format(double(r), 8, -126, 127, 8));
+      else static_cast<uint16_t*>(x)[k] = uint16_t(round_to_format(double(r), 11, -14, 15, 5));
+    }
+    advance_tuple(t.data(), xshape, dim);
+  }
+}
+
 // Views of y starting at the tuple `ystart` (Section 4: the slice's flat index is the
 // tensor's flat index of the start tuple -- its bias -- plus the flat index of the tuple
 // within the slice, both by Horner's rule on y's own shape).  The tuples t walk x's shape

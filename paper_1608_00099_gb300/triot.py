@@ -67,6 +67,7 @@ def lib() -> C.CDLL:
             "triot_moment_workspace_size": (i, [i, _I64P, i, C.POINTER(sz)]),
             "triot_moment": (i, [i, _I64P, vp, i, vp, vp, sz, vp]),
             "triot_moment_noalloc": (i, [i, _I64P, vp, i, vp, vp]),
+            "triot_apply": (i, [i, i, _I64P, vp, _I64P, vp, _I64P, vp, i, vp]),
             "triot_embed_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, u, vp]),
             "triot_crop_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
             "triot_product_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
@@ -185,6 +186,16 @@ def triot_moment(p: torch.Tensor, out: torch.Tensor | None = None, workspace: to
     _check(lib().triot_moment(rank, _shape(p.shape), _dev(p), _dtype(p), _dev(out), _dev(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
     return out
+
+
+APPLY_XPYXMZ = 1
+
+
+def triot_apply_xpyxmz(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, stream=None) -> torch.Tensor:
+    """x[t] <- x[t] + y[t] * x[t] - z[t] over x's shape (y and z contain it), in place."""
+    _check(lib().triot_apply(APPLY_XPYXMZ, x.dim(), _shape(x.shape), _dev(x), _shape(y.shape), _dev(y),
+                             _shape(z.shape), _dev(z), _dtype(x), _stream(stream)))
+    return x
 
 
 def triot_embed_at(x: torch.Tensor, y: torch.Tensor, ystart, flags: int = 0, stream=None) -> torch.Tensor:

@@ -44,6 +44,10 @@ MUTANTS = [
     ("view bias computed with x's shape", "const u64 bias = tuple_to_index(ystart, yshape, dim);",
      "const u64 bias = tuple_to_index(ystart, xshape, dim);",
      [lambda o: pins.test_views_against_numpy_slicing(o, "f64", 1)]),
+    ("benchmark 3 reads z with y's shape",
+     "const u64 iy = tuple_to_index(t.data(), yshape, dim), iz = tuple_to_index(t.data(), zshape, dim);",
+     "const u64 iy = tuple_to_index(t.data(), yshape, dim), iz = tuple_to_index(t.data(), yshape, dim);",
+     [lambda o: pins.test_apply_xpyxmz_against_numpy(o, "f64", 0)]),
     ("bf16 product rounds with f16 parameters",
      "yy[iy] = uint16_t(round_to_format(exact, 8, -126, 127, 8));",
      "yy[iy] = uint16_t(round_to_format(exact, 11, -14, 15, 5));",

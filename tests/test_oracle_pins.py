@@ -398,6 +398,52 @@ def test_moment_nonfinite_is_the_plain_ieee_sum(orc, nthreads):
             assert (np.isnan(g_) and np.isnan(w_)) or g_ == w_, (bad, got)
 
 
+# ---------------------------------------------------------------- benchmark 3: x <- x + y x - z
+
+APPLY_CASES = [((3, 4), (5, 7), (4, 9)), ((2, 3, 4), (2, 3, 4), (3, 5, 6)), ((5,), (9,), (5,)),
+               ((3, 2, 2, 2), (4, 3, 5, 7), (8, 2, 6, 3))]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", range(len(APPLY_CASES)))
+def test_apply_xpyxmz_against_numpy(orc, dtype, case):
+    xs, ys, zs = APPLY_CASES[case]
+    rng = np.random.default_rng(95 + case)
+    vals = [rng.standard_normal(int(np.prod(s))) for s in (xs, ys, zs)]
+    if dtype != "f64":
+        vals = [orc.from_f64(v, dtype) for v in vals]
+    x, y, z = vals
+    got = orc.apply_xpyxmz(x, xs, y, ys, z, zs, dtype)
+    sl = tuple(slice(0, e) for e in xs)
+    if dtype in ("f64", "f32"):
+        ft = np.float64 if dtype == "f64" else np.float32
+        X = x.reshape(xs).astype(ft)
+        Y = y.reshape(ys)[sl].astype(ft)
+        Z = z.reshape(zs)[sl].astype(ft)
+        want = np.subtract(np.add(X, np.multiply(Y, X)), Z)
+        assert got.tobytes() == want.astype(ft).tobytes()
+    else:
+        X = orc.to_f64(x, dtype).reshape(xs).astype(np.float32)
+        Y = orc.to_f64(y, dtype).reshape(ys)[sl].astype(np.float32)
+        Z = orc.to_f64(z, dtype).reshape(zs)[sl].astype(np.float32)
+        r = np.subtract(np.add(X, np.multiply(Y, X)), Z)
+        if dtype == "f16":
+            want = r.astype(np.float16).view(np.uint16)
+        else:
+            want = torch.from_numpy(np.ascontiguousarray(r)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        assert got.tobytes() == np.ascontiguousarray(want).tobytes()
+
+
+def test_apply_xpyxmz_special_cases(orc):
+    xs, ys = (3, 4), (5, 6)
+    x = np.random.default_rng(99).standard_normal(12)
+    zero_y, zero_z = np.zeros(30), np.zeros(30)
+    assert orc.apply_xpyxmz(x, xs, zero_y, ys, zero_z, ys, "f64").tobytes() == x.tobytes()  # x unchanged
+    ones = np.ones(30)
+    got = orc.apply_xpyxmz(x, xs, ones, ys, ones, ys, "f64")
+    assert got.tobytes() == ((x + x) - 1.0).tobytes()                                       # 2x - 1
+
+
 # ---------------------------------------------------------------- views (Section 4 bias)
 
 VIEW_CASES = [((2, 3), (5, 7), (1, 4)), ((3, 1, 4), (6, 2, 9), (2, 1, 5)), ((4,), (4,), (0,)),
