@@ -467,6 +467,17 @@ def run_extra_workloads(args, triot, synth, dev, stream):
         res[f"precision_{name}"] = r
         del P, Q, R
     torch.cuda.empty_cache()
+    # benchmark 4 of Section 3: naive convolution of two (2^8, 2^3) f64 matrices; |a| |b|
+    # multiply-adds (compute-bound: reported in GFLOP/s against the nominal FP64 rate)
+    ca, cb = (2 ** 8, 2 ** 3), (2 ** 8, 2 ** 3)
+    A4 = torch.from_numpy(synth.normal01(1010, 2048).reshape(ca)).to(dev)
+    B4 = torch.from_numpy(synth.normal01(1011, 2048).reshape(cb)).to(dev)
+    O4 = torch.empty([x + y - 1 for x, y in zip(ca, cb)], dtype=torch.float64, device=dev)
+    ms = time_op(lambda k, st: triot.triot_convolve(A4, B4, out=O4, stream=st), 50, stream)
+    flops = 2.0 * 2048 * 2048
+    res["convolve_benchmark4_f64"] = {"convolve": {"us": round(ms * 1e3, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                                                   "frac_nominal_fp64": round(flops / (ms * 1e-3) / 1.25e12, 4)}}
+    del A4, B4, O4
     # benchmark 3 of Section 3 on the paper's shapes, f64: x <- x + y x - z over x's shape;
     # 4 * 8 * |x| bytes per call, copies rotated so the touched data exceeds 4x L2
     bx = (2 ** 7 + 1, 2 ** 5, 2 ** 3 + 5, 2 ** 4)

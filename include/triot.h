@@ -101,6 +101,20 @@ int triot_product(int rank, const int64_t* xshape, const void* x, const int64_t*
                   void* y, int dtype, void* stream);
 
 /*
+ * triot_convolve -- naive multidimensional convolution (Algorithms 14 and 15; Section 3,
+ *   benchmark 4): out[t] = sum of a[u] * b[t - u] over the tuples u of a's shape for which
+ *   t - u is a tuple of b's shape, for every tuple t of the result shape
+ *   ashape + bshape - 1 (dense row-major, written entirely; an axis of extent 0 in a or b
+ *   gives an all-zero result on that extent).  dtype must be TRIOT_F64.  Each product is
+ *   rounded, then the products of an output are summed in a fixed order (32 partial sums
+ *   over the outermost axis, combined pairwise), so the result differs from the paper's
+ *   scatter order only by rounding and is identical from run to run.  out must not overlap
+ *   a or b.
+ */
+int triot_convolve(int rank, const int64_t* ashape, const void* a, const int64_t* bshape,
+                   const void* b, void* out, int dtype, void* stream);
+
+/*
  * triot_apply -- an elementwise operation over three tensors of different shapes, visiting
  *   every tuple t of x's shape (Algorithm 9's apply with several tensors).  The fixed set of
  *   operations:

@@ -68,6 +68,7 @@ def lib() -> C.CDLL:
             "triot_moment": (i, [i, _I64P, vp, i, vp, vp, sz, vp]),
             "triot_moment_noalloc": (i, [i, _I64P, vp, i, vp, vp]),
             "triot_apply": (i, [i, i, _I64P, vp, _I64P, vp, _I64P, vp, i, vp]),
+            "triot_convolve": (i, [i, _I64P, vp, _I64P, vp, vp, i, vp]),
             "triot_embed_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, u, vp]),
             "triot_crop_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
             "triot_product_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
@@ -185,6 +186,19 @@ def triot_moment(p: torch.Tensor, out: torch.Tensor | None = None, workspace: to
         raise TriotError(8, "out must hold rank + 1 float64 values")
     _check(lib().triot_moment(rank, _shape(p.shape), _dev(p), _dtype(p), _dev(out), _dev(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
+    return out
+
+
+def triot_convolve(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Naive multidimensional convolution of two f64 tensors of one rank; out has shape
+    a.shape + b.shape - 1."""
+    shape = [max(0, x + y - 1) for x, y in zip(a.shape, b.shape)]
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=a.device)
+    if list(out.shape) != shape:
+        raise TriotError(8, f"out must have shape {shape}")
+    _check(lib().triot_convolve(a.dim(), _shape(a.shape), _dev(a), _shape(b.shape), _dev(b), _dev(out),
+                                _dtype(a), _stream(stream)))
     return out
 
 

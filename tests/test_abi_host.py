@@ -141,6 +141,10 @@ def test_bad_arguments_fail_before_any_gpu_work(tr):
     assert L.triot_moment_product(3, 2, neg, ptrs, 0, fake2, fake2, 1 << 20, None) == 2
     nbytes = C.c_size_t(0)
     assert L.triot_moment_product_workspace_size(3, 0, shp, 0, C.byref(nbytes)) == 8
+    # convolution: f64 only, rank, shapes
+    assert L.triot_convolve(3, s3, fake, s3, fake2, fake, 1, None) == 4
+    assert L.triot_convolve(0, s3, fake, s3, fake2, fake, 0, None) == 1
+    assert L.triot_convolve(3, tr._shape((2, -1, 4)), fake, s3, fake2, fake, 0, None) == 2
     # apply: op code, shapes (y and z contain x)
     assert L.triot_apply(9, 3, s3, fake, s3, fake2, s3, fake2, 0, None) == 8
     assert L.triot_apply(1, 3, big, fake, s3, fake2, big, fake2, 0, None) == 2
