@@ -95,7 +95,9 @@ int launch_rows(int op, int rank, const int64_t* xshape, const void* x, const in
   const void* B = (op == ROW_CROP) ? y : x;
   RowLaunch L;
   plan_rows(op, c, x_empty, es, A, B, flags, t, dev, L);
-  const void* fn = (op == ROW_EMBED) ? embed_kernel_ptr(es, L.g.nouter)
+  if (op == ROW_CROP && !L.g.a_dense) return fail(TRIOT_ERR_ARG, "internal: crop into a strided tensor");
+  const void* fn = (op == ROW_EMBED) ? (L.g.a_dense ? embed_kernel_ptr(es, L.g.nouter)
+                                                    : embed_view_kernel_ptr(es, L.g.nouter))
                    : (op == ROW_CROP) ? crop_kernel_ptr(es, L.g.nouter)
                                       : product_kernel_ptr(dtype, L.g.nouter);
   if (!fn) return fail(TRIOT_ERR_RANK, "no kernel for this effective rank");

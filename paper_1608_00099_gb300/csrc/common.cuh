@@ -36,7 +36,9 @@ __host__ __device__ constexpr int b64_dyn_smem(int b, int DO) {
          kB64Warps * 32 * (b64_levels(DO) * 20 + b64_qlevels(DO) * 16 + DO * 8);
 }
 
-enum RowOp { ROW_EMBED = 0, ROW_CROP = 1, ROW_PRODUCT = 2 };
+// ROW_EMBED_S: embed into a view of a larger tensor (A's row offsets from its strides); a
+// separate instantiation so that the dense embed's row decode carries no extra branch
+enum RowOp { ROW_EMBED = 0, ROW_CROP = 1, ROW_PRODUCT = 2, ROW_EMBED_S = 3 };
 
 // Element types of the kernels.
 enum Dtype { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, DT_F16 = 3 };
@@ -91,7 +93,7 @@ struct RowGeom {
   int rows32;                      // rows fit the 32-bit decode
   int nopad;                       // embed: skip writing the pad
   int a_dense;                     // A's rows lie back to back (offset = row * inner); 0 for
-                                   // a view of a larger tensor (offsets from the strides)
+                                   // a view of a larger tensor (host: selects ROW_EMBED_S)
 };
 
 enum {

@@ -6,6 +6,8 @@ namespace triot {
 // row kernels: op ROW_EMBED / ROW_CROP by element size (2, 4, 8 bytes), ROW_PRODUCT by
 // dtype; nouter = effective rank - 1 in [0, 23]
 const void* embed_kernel_ptr(int es, int nouter);
+// embed into a view whose written rows are not back to back (strided A)
+const void* embed_view_kernel_ptr(int es, int nouter);
 const void* crop_kernel_ptr(int es, int nouter);
 const void* product_kernel_ptr(int dtype, int nouter);
 // moment kernels by dtype and effective rank D in [1, 24]; m > 0 selects the block-column

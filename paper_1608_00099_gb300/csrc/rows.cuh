@@ -64,8 +64,10 @@ __device__ __forceinline__ __nv_bfloat16 mul_rn(__nv_bfloat16 a, __nv_bfloat16 b
 // Flat row index -> offsets of the row in A and B (and, for embed, whether the row's
 // tuple lies inside x).  Digits are peeled innermost first as in Algorithm 4; each digit
 // multiplies the tensor's stride for that axis.
-template <int OP, int NOUT>
-__device__ __forceinline__ RowInfo decode_row(const RowGeom& g, long long r) {
+template <int OP, int NOUT, bool AS>
+__device__ __forceinline__ RowInfo decode_row_impl(const RowGeom& g, long long r) {
+  // AS: A's row offset from its strides (the product, or a view of a larger tensor);
+  // otherwise A is dense and its row offset is r * inner
   long long oa = 0, ob = 0;
   bool inside = true;
   if (g.rows32) {
@@ -80,9 +82,9 @@ __device__ __forceinline__ RowInfo decode_row(const RowGeom& g, long long r) {
       } else {
         t = rem;
       }
-      if (OP == ROW_PRODUCT || !g.a_dense) oa += (long long)t * g.sa[k];
+      if (AS) oa += (long long)t * g.sa[k];
       ob += (long long)t * g.sb[k];
-      if (OP == ROW_EMBED) inside = inside && ((long long)t < g.bound[k]);
+      if ((OP == ROW_EMBED || OP == ROW_EMBED_S)) inside = inside && ((long long)t < g.bound[k]);
     }
   } else {
     long long rem = r;
@@ -96,15 +98,20 @@ __device__ __forceinline__ RowInfo decode_row(const RowGeom& g, long long r) {
       } else {
         t = rem;
       }
-      if (OP == ROW_PRODUCT || !g.a_dense) oa += t * g.sa[k];
+      if (AS) oa += t * g.sa[k];
       ob += t * g.sb[k];
-      if (OP == ROW_EMBED) inside = inside && (t < g.bound[k]);
+      if ((OP == ROW_EMBED || OP == ROW_EMBED_S)) inside = inside && (t < g.bound[k]);
     }
   }
   RowInfo ri;
-  ri.a = (OP == ROW_PRODUCT || !g.a_dense) ? oa : r * g.inner;
-  ri.b = (OP == ROW_EMBED && !inside) ? -1 : ob;
+  ri.a = AS ? oa : r * g.inner;
+  ri.b = ((OP == ROW_EMBED || OP == ROW_EMBED_S) && !inside) ? -1 : ob;
   return ri;
+}
+
+template <int OP, int NOUT>
+__device__ __forceinline__ RowInfo decode_row(const RowGeom& g, long long r) {
+  return decode_row_impl<OP, NOUT, OP == ROW_PRODUCT || OP == ROW_EMBED_S>(g, r);
 }
 
 // element-level work of one op on one element, scalar
@@ -112,7 +119,7 @@ template <int OP, typename T>
 __device__ __forceinline__ void row_elem(const RowGeom& g, T* __restrict__ A,
                                          const T* __restrict__ B, const RowInfo& ri,
                                          long long c) {
-  if constexpr (OP == ROW_EMBED) {
+  if constexpr ((OP == ROW_EMBED || OP == ROW_EMBED_S)) {
     const bool in = ri.b >= 0 && c < g.b_inner;
     if (in) A[ri.a + c] = B[ri.b + c];
     else if (!g.nopad) A[ri.a + c] = T(0);
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(1024) rows_kernel(const __grid_constant__ RowG
         for (int u = 0; u < U; ++u) {
           if (!ok[u]) continue;
           if constexpr (OP == ROW_PRODUCT) va[u] = ld16(A + ri[u].a + c[u]);
-          if constexpr (OP == ROW_EMBED) {
+          if constexpr ((OP == ROW_EMBED || OP == ROW_EMBED_S)) {
             if (ri[u].b >= 0 && c[u] < g.b_inner) {
               if (g.path == PATH_VEC) {
                 vb[u] = ld16(B + ri[u].b + c[u]);
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(1024) rows_kernel(const __grid_constant__ RowG
 #pragma unroll
             for (int j = 0; j < VEC; ++j) o.v[j] = mul_rn(va[u].v[j], vb[u].v[j]);
             st16(dst, o);
-          } else if (OP == ROW_EMBED && g.nopad) {
+          } else if ((OP == ROW_EMBED || OP == ROW_EMBED_S) && g.nopad) {
             if (ri[u].b >= 0 && c[u] < g.b_inner) {
               if (c[u] + VEC <= g.b_inner) {
                 st16(dst, vb[u]);
