@@ -1,5 +1,6 @@
-// Host planning: validation (check_tensor_pack_bounds, Algorithm 8), canonicalisation
-// (Section 4: trivial axes are ignored; contiguous neighbours merge) and tiling.
+// Host planning of the row operations (embed, crop, product): validation
+// (check_tensor_pack_bounds, Algorithm 8), canonicalisation (Section 4: trivial axes are
+// ignored; contiguous neighbours merge) and tiling.
 #include "plan.h"
 
 #include <algorithm>
@@ -21,11 +22,6 @@ void strides_of(int rank, const int64_t* shape, int64_t* st) {
 
 bool mul_overflows(int64_t a, int64_t b) {
   return a != 0 && b > INT64_MAX / a;
-}
-
-long long gcd_ll(long long a, long long b) {
-  while (b) { long long t = a % b; a = b; b = t; }
-  return a;
 }
 
 }  // namespace
@@ -120,50 +116,6 @@ int canon_rows(int op, int rank, const int64_t* xshape, const int64_t* yshape, C
   c.D = D;
   return TRIOT_OK;
 }
-
-int canon_moment(int rank, const int64_t* shape, Canon& c, std::string& err) {
-  char buf[256];
-  if (rank < 1 || rank > kMaxRank) {
-    snprintf(buf, sizeof buf, "rank %d outside [1, %d]", rank, kMaxRank);
-    err = buf;
-    return TRIOT_ERR_RANK;
-  }
-  if (!shape) { err = "shape pointer is NULL"; return TRIOT_ERR_NULL; }
-  c = Canon();
-  c.total = 1;
-  for (int i = 0; i < rank; ++i) {
-    if (shape[i] < 0) {
-      snprintf(buf, sizeof buf, "negative extent on axis %d", i);
-      err = buf;
-      return TRIOT_ERR_SHAPE;
-    }
-    if (shape[i] >= (int64_t(1) << 31)) {
-      snprintf(buf, sizeof buf, "moment axis %d extent %lld must be < 2^31", i, (long long)shape[i]);
-      err = buf;
-      return TRIOT_ERR_SHAPE;
-    }
-    if (mul_overflows(c.total, shape[i])) { err = "element count overflows int64"; return TRIOT_ERR_SHAPE; }
-    c.total *= shape[i];
-  }
-  c.empty = (c.total == 0);
-  int D = 0;
-  for (int i = 0; i < rank; ++i) {
-    if (shape[i] == 1) continue;
-    c.ext[D] = shape[i];
-    c.orig[D] = i;
-    c.sa[D] = c.sb[D] = 0;
-    c.bound[D] = shape[i];
-    ++D;
-  }
-  if (D == 0) {  // a single element: its tuple is all zeros
-    c.ext[0] = 1;
-    c.orig[0] = 0;
-    D = 1;
-  }
-  c.D = D;
-  return TRIOT_OK;
-}
-
 void plan_rows(int op, const Canon& c, bool x_empty, int es, const void* A, const void* B,
                unsigned flags, const TuneCfg& t, const DeviceInfo& dev, RowLaunch& L) {
   RowGeom& g = L.g;
@@ -246,120 +198,6 @@ void plan_rows(int op, const Canon& c, bool x_empty, int es, const void* A, cons
   L.grid = (int)std::max(1ll, grid);
   L.block = threads;
   L.smem = (size_t)g.rows_per_tile * sizeof(RowInfo);
-}
-
-long long moment_segment(const Canon& c, int es, long long target_lanes) {
-  // A lane segment is a whole number of 128-byte chunks.  When it is also a multiple of
-  // the inner extent L (and of L * s_{D-2}), every lane of a warp reaches its row ends
-  // (and the next carries) at the same step, so the carry code runs without divergence.
-  // Each segment costs a tuple decode and a flush of D levels (~24 D instructions), so
-  // segments are preferably at least 24 D elements long -- unless the tensor is too small
-  // to give every lane of a full GPU some work, in which case parallelism wins.
-  const long long C = 128 / es;
-  const long long L = c.ext[c.D - 1];
-  auto lcm = [](long long a, long long b) { return a / gcd_ll(a, b) * b; };
-  const long long base0 = (L > 0 && lcm(C, L) <= 4096) ? lcm(C, L) : C;
-  long long base1 = base0;
-  if (c.D >= 2 && L > 0) {
-    const long long blk = L * c.ext[c.D - 2];
-    if (blk > 0 && blk <= 4096 && lcm(C, blk) <= 4096) base1 = lcm(C, blk);
-  }
-  const long long smin = std::max(C, 24ll * c.D);
-  auto up = [&](long long b, long long lo) { return (lo + b - 1) / b * b; };
-  const long long cands[4] = {up(base1, smin), up(base0, smin), base0, C};
-  for (long long s : cands)
-    if (c.total >= s * target_lanes) return s;
-  // too small for every lane: the largest chunk multiple that still fills the lanes
-  long long s = (c.total / std::max(1ll, target_lanes)) / C * C;
-  return std::max(C, s);
-}
-
-int moment_block_axes(const Canon& c, int dtype) {
-  (void)dtype;
-  long long b = 1;
-  int m = 0;
-  for (int a = c.D - 1; a >= 0; --a) {
-    if (b * c.ext[a] > 16) break;
-    b *= c.ext[a];
-    ++m;
-  }
-  return m;
-}
-
-void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
-                 const DeviceInfo& dev, int occ, MomentLaunch& L) {
-  MomentGeom& g = L.g;
-  g = MomentGeom();
-  const int D = c.D;
-  g.D = D;
-  g.n = c.total;
-  for (int i = 0; i < D; ++i) {
-    g.ext[i] = c.ext[i];
-    g.div[i] = make_fastdiv((uint32_t)c.ext[i]);
-  }
-  g.n32 = c.total < (int64_t(1) << 32);
-  g.aligned = (reinterpret_cast<uintptr_t>(p) % 16) == 0;
-  const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
-  const long long max_ctas = (long long)dev.sms * std::max(1, cps);
-  const int warps = (m > 0 && es == 8) ? kB64Warps : m > 0 ? kMomentBlkWarps : kMomentWarps;
-  L.warps = warps;
-  const long long target_lanes = max_ctas * warps * 32;
-  const long long C = 128 / es;
-  g.m = m;
-  if (m > 0 && es == 8) {
-    // f64 blocks: rounds of 32 chunks of K whole blocks each; every warp takes a contiguous
-    // share of the rounds (the kernel splits them evenly), one chunk per lane and round
-    long long B = 1;
-    for (int a = D - m; a < D; ++a) B *= c.ext[a];
-    g.B = (int)B;
-    const long long CB = (long long)b64_blocks_per_chunk((int)B) * B;
-    g.seg = CB;
-    g.nchunks = 1;
-    g.nround = (c.total + 32 * CB - 1) / (32 * CB);
-    // a window: at most kB64Window elements per lane and 512 per block column (a column sum
-    // of 512 elements below 2^53 stays below 2^62)
-    g.win = (int)std::max(1ll, std::min((long long)kB64Window, 512 * B) / CB);
-  } else if (m > 0) {
-    long long B = 1;
-    for (int a = D - m; a < D; ++a) B *= c.ext[a];
-    g.B = (int)B;
-    // segments: whole blocks, 16-byte aligned starts; long enough to amortise the decode
-    // and flush of the D - m outer levels and the B column folds, unless that starves lanes
-    const long long al = 16 / es;
-    const long long base = B / gcd_ll(B, al) * al;
-    const long long smin = 24ll * (D - m) + 8ll * B + C;
-    long long S = (smin + base - 1) / base * base;
-    if (c.total < S * target_lanes) {
-      const long long fill = (c.total / std::max(1ll, target_lanes)) / base * base;
-      S = std::max(base, std::min(S, fill));
-    }
-    // align segments to whole blocks of the innermost outer axes as far as S allows, so
-    // the lanes of a warp wrap those digits at the same step (carries without divergence)
-    long long align = B;
-    for (int a = D - m - 1; a >= 0; --a) {
-      if (align * c.ext[a] > S) break;
-      align *= c.ext[a];
-    }
-    const long long align2 = align / gcd_ll(align, al) * al;
-    if (S >= align2) S = S / align2 * align2;
-    g.seg = S;
-    g.nchunks = (int)((S + C - 1) / C);
-  } else {
-    g.B = 0;
-    g.seg = moment_segment(c, es, target_lanes);
-    g.nchunks = (int)(g.seg / C);
-  }
-  g.nwarpseg = c.empty ? 0 : (c.total + 32 * g.seg - 1) / (32 * g.seg);
-  long long need = (g.nwarpseg + warps - 1) / warps;
-  long long grid = std::min(need, max_ctas);
-  L.empty = c.empty;
-  L.grid = c.empty ? 0 : (int)std::max(1ll, grid);
-  CombineGeom& cg = L.cg;
-  cg = CombineGeom();
-  cg.D = D;
-  cg.rank = rank;
-  cg.nparts = L.grid;
-  for (int i = 0; i < D; ++i) cg.orig[i] = c.orig[i];
 }
 
 }  // namespace triot
