@@ -258,210 +258,6 @@ __global__ void __launch_bounds__(kMomentWarps * 32) moment_f32_kernel(
   }
 }
 
-// ====================================================================== f32, short rows
-//
-// Block-column mode, for inner extents of at most kBlkMax elements.  The last m axes form
-// a block of B <= kBlkMax elements and lane segments are whole numbers of blocks.  An
-// element at position j of its block adds its value to the lane's column sum cs[j] (shared
-// memory) and to the block's mass; at a block end the block's mass is carried up the
-// DO = D - m outer axes exactly as a row's mass is in row mode.  The inner axes need no
-// per-element work at all: at the end, m_a = sum_j digit_a(j) * colsum[j] for each of the m
-// block axes.  Column sums are folded into compensated f32 pairs at each segment end, so
-// no plain f32 sum runs over more than one segment.
-constexpr int kBlkMax = 16;
-constexpr int kColStride = kBlkMax + 1;  // odd stride: lanes at the same column hit distinct banks
-constexpr int kBlkWarps = kMomentBlkWarps;  // warps per CTA (keeps static shared memory < 48 KB)
-
-template <typename T, int DO>
-__global__ void __launch_bounds__(kBlkWarps * 32) moment_blk_kernel(
-    const __grid_constant__ MomentGeom g, const T* __restrict__ p, double* __restrict__ partial) {
-  constexpr int ES = sizeof(T);
-  constexpr int C = 128 / ES;
-  constexpr int NO = DO > 0 ? DO : 1;
-  __shared__ __align__(16) unsigned char stage[kBlkWarps][2][kStageBytes];
-  __shared__ float s_cs[kBlkWarps][32][kColStride];       // current segment
-  __shared__ float s_ch[kBlkWarps][32][kColStride];       // folded: value
-  __shared__ float s_ce[kBlkWarps][32][kColStride];       // folded: compensation
-  __shared__ double wsum[kBlkWarps][kMaxRank + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * kBlkWarps + warp;
-  const long long tw = (long long)gridDim.x * kBlkWarps;
-  const long long nseg = gw < g.nwarpseg ? (g.nwarpseg - gw + tw - 1) / tw : 0;
-  const long long nsteps = nseg * g.nchunks;
-  const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
-  const int B = g.B, m = g.m;
-  float* cs = s_cs[warp][lane];
-  float* ch = s_ch[warp][lane];
-  float* ce = s_ce[warp][lane];
-  for (int j = 0; j < B; ++j) { cs[j] = 0.f; ch[j] = 0.f; ce[j] = 0.f; }
-
-  Comp32 A[NO], P[NO + 1];  // A[i]: outer axis i; P[0]: mass; P[k]: pending of level k-1
-#pragma unroll
-  for (int i = 0; i < NO; ++i) A[i].zero();
-#pragma unroll
-  for (int i = 0; i <= NO; ++i) P[i].zero();
-  uint32_t t[NO];
-#pragma unroll
-  for (int i = 0; i < NO; ++i) t[i] = 0;
-  float bm = 0.f;  // mass of the current block
-  int jb = 0;      // position in the current block
-  bool active = false;
-
-  auto block_end = [&]() {
-    if (DO == 0) {
-      P[0].add(bm);
-    } else {
-      P[DO].s = bm;
-      P[DO].e = 0.f;
-#pragma unroll
-      for (int i = DO - 1; i >= 0; --i) {
-        const float pm = P[i + 1].value();
-        A[i].add((float)t[i] * pm);
-        P[i].add(pm);
-        P[i + 1].zero();
-        if (i > 0) {
-          if (++t[i] < (uint32_t)g.ext[i]) break;
-          t[i] = 0;
-        } else {
-          ++t[0];
-        }
-      }
-    }
-    bm = 0.f;
-  };
-  auto flush_levels = [&]() {
-#pragma unroll
-    for (int i = DO - 2; i >= 0; --i) {
-      const float pm = P[i + 1].value();
-      A[i].add((float)t[i] * pm);
-      P[i].add(pm);
-      P[i + 1].zero();
-    }
-    for (int j = 0; j < B; ++j) {  // fold this segment's column sums
-      const float v = cs[j], s0 = ch[j];
-      const float tt = s0 + v, bp = tt - s0;
-      ce[j] += (s0 - (tt - bp)) + (v - bp);
-      ch[j] = tt;
-      cs[j] = 0.f;
-    }
-  };
-
-  if (nsteps > 0) {
-    stage_chunk<ES>(g, pb, stage[warp][0], gw, 0, lane);
-    cp_async_commit();
-  }
-  for (long long s = 0; s < nsteps; ++s) {
-    const long long ws = gw + (s / g.nchunks) * tw;
-    const int chunk = (int)(s % g.nchunks);
-    if (s + 1 < nsteps) {
-      const long long ws1 = gw + ((s + 1) / g.nchunks) * tw;
-      stage_chunk<ES>(g, pb, stage[warp][(s + 1) & 1], ws1, (int)((s + 1) % g.nchunks), lane);
-    }
-    cp_async_commit();
-    cp_async_wait1();
-    __syncwarp();
-    if (chunk == 0) {
-      const long long k0 = (ws * 32 + lane) * g.seg;
-      active = k0 < g.n;
-      if (active && DO > 0) {
-        // outer digits of the segment's first block (segments start on block boundaries)
-        long long rem = k0 / B;
-        if (g.n32) {
-          uint32_t r32 = (uint32_t)rem;
-#pragma unroll
-          for (int i = DO - 1; i >= 1; --i) {
-            const uint32_t q = fdiv(r32, g.div[i]);
-            t[i] = r32 - q * g.div[i].d;
-            r32 = q;
-          }
-          t[0] = r32;
-        } else {
-#pragma unroll
-          for (int i = DO - 1; i >= 1; --i) {
-            const long long q = rem / g.ext[i];
-            t[i] = (uint32_t)(rem - q * g.ext[i]);
-            rem = q;
-          }
-          t[0] = (uint32_t)rem;
-        }
-      }
-      jb = 0;
-    }
-    if (active) {
-      const unsigned char* row = stage[warp][s & 1] + lane * kStageRowBytes;
-      const long long left = g.seg - (long long)chunk * C;
-      const int cnt = left < C ? (int)left : C;
-      // runs up to the next block end: the carry code has a single call site
-      int j = 0;
-      while (j < cnt) {
-        const int n = (B - jb) < (cnt - j) ? (B - jb) : (cnt - j);
-        for (int k = 0; k < n; ++k) {
-          const float x = elem_f32<T>(row, j + k);
-          cs[jb + k] += x;
-          bm += x;
-        }
-        j += n;
-        jb += n;
-        if (jb == B) {
-          jb = 0;
-          block_end();
-        }
-      }
-      if (chunk == g.nchunks - 1) flush_levels();
-    }
-    __syncwarp();
-  }
-
-  // column sums of the warp: lane j < B adds column j over the 32 lanes (compensated),
-  // then turns it into its contribution to each block axis: digit_a(j) * colsum_j
-  Comp32 Ain[kMaxRank];
-#pragma unroll
-  for (int a = 0; a < kMaxRank; ++a) Ain[a].zero();
-  __syncwarp();
-  if (lane < B) {
-    Comp32 col;
-    col.zero();
-    for (int l = 0; l < 32; ++l) {
-      col.add(s_ch[warp][l][lane]);
-      col.e += s_ce[warp][l][lane];
-    }
-    const float cv = col.value();
-    uint32_t u = (uint32_t)lane;
-    for (int a = DO + m - 1; a >= DO; --a) {  // block axes, innermost digit first
-      const uint32_t e = (uint32_t)g.ext[a];
-      const uint32_t d = u % e;
-      u /= e;
-      Ain[a - DO].add((float)d * cv);
-    }
-  }
-
-  // warp reduction of the compensated pairs (xor butterfly: fixed order); the register
-  // arrays are indexed with compile-time indices only
-  double* ws_out = wsum[warp];
-  const int D = DO + m;
-  auto reduce_out = [&](Comp32 v, int slot) {
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      const float os = __shfl_xor_sync(0xffffffffu, v.s, off);
-      const float oe = __shfl_xor_sync(0xffffffffu, v.e, off);
-      v.add(os);
-      v.e += oe;
-    }
-    if (lane == 0) ws_out[slot] = (double)v.s + (double)v.e;
-  };
-#pragma unroll
-  for (int i = 0; i < DO; ++i) reduce_out(A[i], i);
-  for (int a = 0; a < m; ++a) reduce_out(Ain[a], DO + a);
-  reduce_out(P[0], D);
-  __syncthreads();
-  if (threadIdx.x <= D) {
-    double acc = 0.0;
-#pragma unroll
-    for (int w = 0; w < kBlkWarps; ++w) acc += wsum[w][threadIdx.x];
-    partial[(long long)blockIdx.x * (D + 1) + threadIdx.x] = acc;
-  }
-}
-
 // ====================================================================== f64 fixed point
 //
 // Each lane reads its 16-element chunk from shared memory twice.  First pass: the chunk's

@@ -6,6 +6,7 @@
 #include <cstdio>
 
 #include "../../include/triot.h"
+#include "blk32.cuh"
 
 namespace triot {
 
@@ -117,49 +118,31 @@ void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const T
   g.aligned = (reinterpret_cast<uintptr_t>(p) % 16) == 0;
   const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
   const long long max_ctas = (long long)dev.sms * std::max(1, cps);
-  const int warps = (m > 0 && es == 8) ? kB64Warps : m > 0 ? kMomentBlkWarps : kMomentWarps;
+  const int warps = (m > 0 && es == 8) ? kB64Warps : m > 0 ? kB32Warps : kMomentWarps;
   L.warps = warps;
   const long long target_lanes = max_ctas * warps * 32;
   const long long C = 128 / es;
   g.m = m;
-  if (m > 0 && es == 8) {
-    // f64 blocks: rounds of 32 chunks of K whole blocks each; every warp takes a contiguous
-    // share of the rounds (the kernel splits them evenly), one chunk per lane and round
+  if (m > 0) {
     long long B = 1;
     for (int a = D - m; a < D; ++a) B *= c.ext[a];
+    if (B < 1) B = 1;
     g.B = (int)B;
-    const long long CB = (long long)b64_blocks_per_chunk((int)B) * B;
+    const long long K = es == 8 ? b64_blocks_per_chunk((int)B) : b32_blocks_per_chunk((int)B, es);
+    const long long CB = K * B;
+    // rounds of 32 chunks of K whole blocks each; every warp takes a contiguous share of the
+    // rounds (the kernel splits them evenly), one chunk per lane and round
     g.seg = CB;
     g.nchunks = 1;
     g.nround = (c.total + 32 * CB - 1) / (32 * CB);
-    // a window: at most kB64Window elements per lane and 512 per block column (a column sum
-    // of 512 elements below 2^53 stays below 2^62)
-    g.win = (int)std::max(1ll, std::min((long long)kB64Window, 512 * B) / CB);
-  } else if (m > 0) {
-    long long B = 1;
-    for (int a = D - m; a < D; ++a) B *= c.ext[a];
-    g.B = (int)B;
-    // segments: whole blocks, 16-byte aligned starts; long enough to amortise the decode
-    // and flush of the D - m outer levels and the B column folds, unless that starves lanes
-    const long long al = 16 / es;
-    const long long base = B / gcd_ll(B, al) * al;
-    const long long smin = 24ll * (D - m) + 8ll * B + C;
-    long long S = (smin + base - 1) / base * base;
-    if (c.total < S * target_lanes) {
-      const long long fill = (c.total / std::max(1ll, target_lanes)) / base * base;
-      S = std::max(base, std::min(S, fill));
+    if (es == 8) {
+      // a fixed-point window: at most kB64Window elements per lane and 512 per block column
+      // (a column sum of 512 elements below 2^53 stays below 2^62)
+      g.win = (int)std::max(1ll, std::min((long long)kB64Window, 512 * B) / CB);
+    } else {
+      // a float window: at most kB32Terms blocks per lane
+      g.win = (int)std::max(1ll, (long long)kB32Terms / K);
     }
-    // align segments to whole blocks of the innermost outer axes as far as S allows, so
-    // the lanes of a warp wrap those digits at the same step (carries without divergence)
-    long long align = B;
-    for (int a = D - m - 1; a >= 0; --a) {
-      if (align * c.ext[a] > S) break;
-      align *= c.ext[a];
-    }
-    const long long align2 = align / gcd_ll(align, al) * al;
-    if (S >= align2) S = S / align2 * align2;
-    g.seg = S;
-    g.nchunks = (int)((S + C - 1) / C);
   } else {
     g.B = 0;
     g.seg = moment_segment(c, es, target_lanes);
