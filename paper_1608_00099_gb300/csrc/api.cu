@@ -151,13 +151,17 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
   const void* fn = moment_kernel_ptr(dtype, c.D, m, B);
   if (!fn) return fail(TRIOT_ERR_RANK, "no moment kernel for this effective rank");
   int occ = 1;
-  const bool b64 = m > 0 && dtype == DT_F64, b32 = m > 0 && dtype != DT_F64;
   const int es = dtype_size(dtype), Bk = B < 1 ? 1 : B;
+  const bool b64 = m > 0 && dtype == DT_F64;
+  const bool wb = m > 0 && dtype != DT_F64 && Bk >= 32;
+  const bool b32 = m > 0 && dtype != DT_F64 && Bk < 32;
   const size_t dyn = b64 ? (size_t)b64_dyn_smem(Bk, c.D - m)
-                     : b32 ? (size_t)b32_dyn_smem(Bk, es, c.D - m) : 0;
+                     : b32 ? (size_t)b32_dyn_smem(Bk, es, c.D - m)
+                     : wb ? (size_t)wb_dyn_smem(c.D - m, wb_vec(Bk, es)) : 0;
   const size_t dyn_max = b64 ? (size_t)b64_dyn_smem(Bk, kMaxRank - 1)
-                         : b32 ? (size_t)b32_dyn_smem(Bk, es, kMaxRank - 1) : 0;
-  const int threads = (b64 ? kB64Warps : b32 ? kB32Warps : kMomentWarps) * 32;
+                         : b32 ? (size_t)b32_dyn_smem(Bk, es, kMaxRank - 1)
+                         : wb ? (size_t)wb_dyn_smem(kMaxRank - 1, wb_vec(Bk, es)) : 0;
+  const int threads = (b64 ? kB64Warps : b32 ? kB32Warps : wb ? kWBWarps : kMomentWarps) * 32;
   if ((st = moment_occupancy(fn, threads, dyn, dyn_max, occ))) return st;
   TuneCfg t = force ? *force : tune_lookup(TRIOT_OP_MOMENT, dtype, c);
   plan_moment(c, rank, dtype_size(dtype), m, p, t, dev, occ, L);
@@ -299,11 +303,12 @@ int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q
 int triot_device_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-  int flag = 0, flag2 = 0, flag3 = 0;
+  int flag = 0, flag2 = 0, flag3 = 0, flag4 = 0;
   st_read_device_flag(&flag);
   b64_read_device_flag(&flag2);
   b32_read_device_flag(&flag3);
-  return (flag || flag2 || flag3) ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped") : ok();
+  wb_read_device_flag(&flag4);
+  return (flag || flag2 || flag3 || flag4) ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped") : ok();
 }
 
 }  // extern "C"

@@ -15,10 +15,12 @@ const void* product_kernel_ptr(int dtype, int nouter);
 // m > 0: block-column kernel for blocks of B elements (the last m axes)
 const void* moment_kernel_ptr(int dtype, int D, int m = 0, int B = 0);
 const void* moment_blk32_kernel_ptr(int dtype, int B);
+const void* moment_wb_kernel_ptr(int dtype, int B);
 const void* moment_blk64_kernel_ptr(int B, int DO);
 // sticky flag of the f64 block kernel (a bounded wait gave up); reading clears it
 void b64_read_device_flag(int* flag);
 void b32_read_device_flag(int* flag);
+void wb_read_device_flag(int* flag);
 const void* combine_kernel_ptr();
 // moment of a product of tensors: one kernel per dtype and tensor count (1..4)
 const void* moment_prod_kernel_ptr(int dtype, int ntensors);

@@ -19,7 +19,8 @@
 //
 // Accuracy: every plain f32 sum of a lane runs over at most kB32Terms terms (a window is at
 // most kB32Terms blocks of a lane); at the window end each sum is added across the warp in
-// f32 (a fixed xor tree) and the warp's totals are kept in f64.  Block masses are trees of at
+// f32 (a fixed xor tree) into the warp's compensated f32 totals (two-sum pairs), which are
+// added in f64 at the end.  Block masses are trees of at
 // most 16 elements and the block axes' moments sums of at most 16 products, so every output
 // is within about (kB32Terms + 30) * 2^-24 (5.6e-6) of sum |p| t_i.  Non-finite elements
 // propagate as in a plain sum (an infinite mass times a zero digit gives NaN, as in the
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
   constexpr int NS = kB32Stages;
   constexpr int TH = NW * 32;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ double wtot[NW][kMaxRank + 1];      // the warps' f64 totals
+  __shared__ float wtot[NW][2][kMaxRank + 1];    // the warps' totals: compensated f32 pairs
   __shared__ float s_dig[4][16];                 // digit of block column j on block axis a
   __shared__ uint32_t s_jd[kMaxRank];            // digits of the round jump per outer axis
   __shared__ __align__(8) unsigned long long s_bar[NW][NS];
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int i = 0; i <= kMaxRank; ++i) wtot[warp][i] = 0.0;
+    for (int i = 0; i <= kMaxRank; ++i) wtot[warp][0][i] = wtot[warp][1][i] = 0.f;
   }
   __syncthreads();
 
@@ -296,12 +297,18 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
       jump();
     }
   };
-  // one window sum of every lane into the warp's f64 total (f32 xor tree: a fixed order)
-  double* wt = wtot[warp];
+  // one window sum of every lane into the warp's total (f32 xor tree: a fixed order), kept
+  // as a compensated pair (Knuth's two-sum), so the narrow FP64 pipe is not used per window
+  float* wts = wtot[warp][0];
+  float* wte = wtot[warp][1];
   auto warp_add = [&](float v, int slot) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wt[slot] += (double)v;
+    if (lane == 0) {
+      const float a = wts[slot], t = a + v, bp = t - a;
+      wte[slot] += (a - (t - bp)) + (v - bp);
+      wts[slot] = t;
+    }
   };
   // window end: credit every pending mass, move the window's sums into the warp's totals
   auto end_window = [&]() {
@@ -410,7 +417,11 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
   if (threadIdx.x <= D) {
     double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) acc += wtot[w][threadIdx.x];
+    for (int w = 0; w < NW; ++w) {
+      // a non-finite total carries no meaningful compensation (inf - inf there is NaN)
+      const float ts = wtot[w][0][threadIdx.x], te = wtot[w][1][threadIdx.x];
+      acc += isfinite(ts) ? (double)ts + (double)te : (double)ts;
+    }
     partial[(long long)blockIdx.x * (D + 1) + threadIdx.x] = acc;
   }
 }

@@ -20,7 +20,8 @@ const void* moment_kernel_ptr(int dtype, int D, int m, int B) {
   if (m > 0) {
     if (m > D) return nullptr;
     if (B < 1) B = 1;  // an empty tensor: no launch, any instantiation serves the planner
-    return dtype == DT_F64 ? moment_blk64_kernel_ptr(B, D - m) : moment_blk32_kernel_ptr(dtype, B);
+    if (dtype == DT_F64) return moment_blk64_kernel_ptr(B, D - m);
+    return B >= 32 ? moment_wb_kernel_ptr(dtype, B) : moment_blk32_kernel_ptr(dtype, B);
   }
   auto seq = std::make_integer_sequence<int, kMaxRank>{};
   switch (dtype) {

@@ -92,15 +92,26 @@ long long moment_segment(const Canon& c, int es, long long target_lanes) {
 }
 
 int moment_block_axes(const Canon& c, int dtype) {
-  (void)dtype;
+  // the trailing axes whose product stays within `cap` elements
+  auto axes = [&](long long cap, long long& b) {
+    b = 1;
+    int m = 0;
+    for (int a = c.D - 1; a >= 0; --a) {
+      if (b * c.ext[a] > cap) break;
+      b *= c.ext[a];
+      ++m;
+    }
+    return m;
+  };
   long long b = 1;
-  int m = 0;
-  for (int a = c.D - 1; a >= 0; --a) {
-    if (b * c.ext[a] > 16) break;
-    b *= c.ext[a];
-    ++m;
+  if (dtype != DT_F64) {
+    // float storage: warp blocks of up to 256 elements when the trailing axes reach 128
+    // elements or form whole 512-byte rows (shorter warp blocks leave lanes idle and lose
+    // to the chunked kernel's blocks of at most 16)
+    const int m = axes((long long)kWBMaxC * 32, b);
+    if (b >= 128 || (b >= 32 && wb_vec((int)b, dtype_size(dtype)))) return m;
   }
-  return m;
+  return axes(16, b);
 }
 
 void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
@@ -118,11 +129,35 @@ void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const T
   g.aligned = (reinterpret_cast<uintptr_t>(p) % 16) == 0;
   const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
   const long long max_ctas = (long long)dev.sms * std::max(1, cps);
-  const int warps = (m > 0 && es == 8) ? kB64Warps : m > 0 ? kB32Warps : kMomentWarps;
+  long long Bm = 1;  // block size (block modes)
+  for (int a = D - m; a < D; ++a) Bm *= c.ext[a];
+  const bool wb = m > 0 && es != 8 && Bm >= 32;
+  const int warps = (m > 0 && es == 8) ? kB64Warps : wb ? kWBWarps : m > 0 ? kB32Warps : kMomentWarps;
   L.warps = warps;
   const long long target_lanes = max_ctas * warps * 32;
   const long long C = 128 / es;
   g.m = m;
+  if (wb) {
+    // warp blocks: each warp a contiguous range of whole blocks (g.nround counts blocks),
+    // steps of U = g.nchunks blocks (at most kWBStepBytes), windows of kWBTerms blocks
+    g.B = (int)Bm;
+    g.nround = c.total / Bm;
+    g.win = kWBTerms;
+    g.seg = Bm;
+    g.nchunks = (int)std::max(1ll, (long long)kWBStepBytes / (Bm * es));
+    const long long units = (g.nround + g.nchunks - 1) / g.nchunks;
+    g.nwarpseg = c.empty ? 0 : units;
+    const long long need = (units + warps - 1) / warps;
+    L.empty = c.empty;
+    L.grid = c.empty ? 0 : (int)std::max(1ll, std::min(need, max_ctas));
+    CombineGeom& cg = L.cg;
+    cg = CombineGeom();
+    cg.D = D;
+    cg.rank = rank;
+    cg.nparts = L.grid;
+    for (int i = 0; i < D; ++i) cg.orig[i] = c.orig[i];
+    return;
+  }
   if (m > 0) {
     long long B = 1;
     for (int a = D - m; a < D; ++a) B *= c.ext[a];

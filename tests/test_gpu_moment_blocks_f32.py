@@ -1,11 +1,13 @@
-"""f32 / bf16 / f16 moment on tensors whose trailing axes form blocks of at most 16 elements.
+"""f32 / bf16 / f16 moment on tensors whose trailing axes form short blocks.
 
-These shapes take the block-column kernel with f32 sums: every block size B = 1..16, one to
-twenty outer axes (carries through several levels, jumps that change cold axes), tails that
-end inside a round, signed, subnormal, non-finite and unaligned input, windows of every
-phase.  The reference is the oracle's compensated f64 sum of the stored values (Algorithms
-10 and 11); the tolerance is the stated FP32-accumulation bound, 1e-5 of sum |p[t]| t_i per
-component (the kernel's own bound is about 5.3e-6).
+These shapes take the block-column kernels with f32 sums: chunked blocks of B = 1..16
+elements and warp blocks of 128..256 (staged, or read with 16-byte loads when a block is a
+whole number of 512-byte rows), one to twenty outer axes (carries through several levels,
+jumps that change cold axes), tails that end inside a round, signed, subnormal, non-finite
+and unaligned input, windows of every phase.  The reference is the oracle's compensated f64
+sum of the stored values (Algorithms 10 and 11); the tolerance is the stated
+FP32-accumulation bound, 1e-5 of sum |p[t]| t_i per component (the kernels' own bounds are
+about 5.6e-6).
 """
 import numpy as np
 import pytest
@@ -55,6 +57,7 @@ BLOCK_SHAPES = [
     (9,) * 6, (17, 19, 23, 14), (4,) * 10, (2,) * 20, (101, 103, 6), (5, 7, 9, 11, 2),
     (3,) * 12, (100003, 10), (31, 37, 41, 8), (3, 5, 7, 4), (2, 3, 1, 5, 1, 3), (61, 67, 11),
     (1, 1, 12), (8191, 1, 1), (999, 15), (3001, 13), (77, 7), (40, 2, 7), (1, 1, 1),
+    (7, 2, 128), (3, 5, 256), (1001, 33), (70, 4, 64), (6, 4, 7, 3, 5, 3, 3, 3, 6, 3),
 ]
 
 
@@ -109,8 +112,8 @@ def test_block_moment_f32_nonfinite(tr, dtype, bad):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
-def test_block_moment_f32_unaligned(tr, dtype):
-    shape = (37, 29, 3)
+@pytest.mark.parametrize("shape", [(37, 29, 3), (9, 4, 4, 4, 4), (5, 8, 32)])
+def test_block_moment_f32_unaligned(tr, dtype, shape):
     n = int(np.prod(shape))
     h = stored(synth.uniform01(74, n), dtype)
     buf = torch.zeros(n + 8, dtype=TORCH[dtype], device="cuda")
