@@ -616,18 +616,37 @@ def run_reference(args, rank, world):
 def profile_op(args):
     """A few calls of one op on its workload, for an ncu capture (no JSON line)."""
     import torch
+    from paper_1608_00099_gb300 import build as tb
     from paper_1608_00099_gb300 import synth, triot
+    tb.build()
     dev = torch.device("cuda", 0)
-    c8 = synth.config_f64_d8()
-    x8 = torch.from_numpy(c8.x_values().reshape(c8.xshape)).to(dev)
-    y8 = torch.from_numpy(c8.yprod_values().reshape(c8.prod_shape)).to(dev)
-    out = torch.empty(len(c8.xshape) + 1, dtype=torch.float64, device=dev)
-    ws = torch.empty(triot.triot_moment_product_workspace_size([c8.xshape, c8.prod_shape], torch.float64) // 8 + 2,
-                     dtype=torch.float64, device=dev)
-    for _ in range(max(1, args.steps)):
-        triot.triot_moment_product([x8, y8], out=out, workspace=ws)
+    n = max(1, args.steps)
+    if args.profile_op == "moment_product_f64_d8":
+        c8 = synth.config_f64_d8()
+        x8 = torch.from_numpy(c8.x_values().reshape(c8.xshape)).to(dev)
+        y8 = torch.from_numpy(c8.yprod_values().reshape(c8.prod_shape)).to(dev)
+        out = torch.empty(len(c8.xshape) + 1, dtype=torch.float64, device=dev)
+        ws = torch.empty(triot.triot_moment_product_workspace_size([c8.xshape, c8.prod_shape], torch.float64) // 8
+                         + 2, dtype=torch.float64, device=dev)
+        for _ in range(n):
+            triot.triot_moment_product([x8, y8], out=out, workspace=ws)
+    else:
+        if args.profile_op == "moment_f32_d24":
+            # the f32 d=24 workload's moment: x of shape (2,)*24, U(0,1)
+            c = synth.config_f32_d24()
+            p = torch.from_numpy(c.x_values().astype(np.float32).reshape(c.xshape)).to(dev)
+        else:
+            # bf16 blocks of 16 under three axes of 200 (the chunked float block kernel)
+            shape = (200, 200, 200, 16)
+            v = synth.uniform01(1010, int(np.prod(shape))).astype(np.float32)
+            p = torch.from_numpy(v.reshape(shape)).to(dev).to(torch.bfloat16)
+        out = torch.empty(p.dim() + 1, dtype=torch.float64, device=dev)
+        ws = torch.empty(triot.triot_moment_workspace_size(tuple(p.shape), p.dtype) // 8 + 2,
+                         dtype=torch.float64, device=dev)
+        for _ in range(n):
+            triot.triot_moment(p, out=out, workspace=ws)
     torch.cuda.synchronize()
-    print(f"{args.profile_op}: {max(1, args.steps)} calls done", flush=True)
+    print(f"{args.profile_op}: {n} calls done", flush=True)
 
 
 def main():
@@ -646,7 +665,8 @@ def main():
     ap.add_argument("--no-big", action="store_true", help="skip the 44 GB f32 d=24 workload")
     ap.add_argument("--autotune", default="", help="autotune the three ops and save the cache here")
     ap.add_argument("--no-tune-file", action="store_true", help="ignore the committed tuning file")
-    ap.add_argument("--profile-op", default="", choices=["", "moment_product_f64_d8"],
+    ap.add_argument("--profile-op", default="",
+                    choices=["", "moment_product_f64_d8", "moment_f32_d24", "moment_bf16_blocks16"],
                     help="only run one op a few times (the command the ncu summaries capture)")
     args = ap.parse_args()
     if args.profile_op:
