@@ -31,14 +31,25 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
       if (!covered) out[k] = 0.0;
     }
   }
+  // the first kCache partials of each thread stay in registers between the two passes
+  // (every launch with at most kCache * kCombineThreads partials reads them once)
+  constexpr int kCache = 4;
+  unsigned long long cb[kCache];
   unsigned emax = 0;
   int bad = 0;
-  for (int k = threadIdx.x; k < g.nparts; k += blockDim.x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(partial[(long long)k * stride + c]);
+  auto scan = [&](unsigned long long b) {
     const unsigned e = (unsigned)((b >> 52) & 0x7FF);
     if (e == 0x7FF) bad = 1;
     else emax = e > emax ? e : emax;
+  };
+#pragma unroll
+  for (int r = 0; r < kCache; ++r) {
+    const int k = threadIdx.x + r * kCombineThreads;
+    cb[r] = k < g.nparts ? (unsigned long long)__double_as_longlong(partial[(long long)k * stride + c]) : 0ull;
+    scan(cb[r]);
   }
+  for (int k = threadIdx.x + kCache * kCombineThreads; k < g.nparts; k += kCombineThreads)
+    scan((unsigned long long)__double_as_longlong(partial[(long long)k * stride + c]));
   emax = __reduce_max_sync(0xffffffffu, emax);
   bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
   if (lane == 0) { s_emax[warp] = emax; s_bad[warp] = bad; }
@@ -56,14 +67,17 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
   }
   const int E = emax ? (int)emax : 1;
   __int128 acc = 0;
-  for (int k = threadIdx.x; k < g.nparts; k += blockDim.x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(partial[(long long)k * stride + c]);
+  auto add = [&](unsigned long long b) {
     const int e = (int)((b >> 52) & 0x7FF);
     const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
     const int sh = kCombineFrac - (E - (e ? e : 1));
     __int128 v = scale_shift((__int128)m, sh);
     acc += (b >> 63) ? -v : v;
-  }
+  };
+#pragma unroll
+  for (int r = 0; r < kCache; ++r) add(cb[r]);  // absent partials are +0 and add nothing
+  for (int k = threadIdx.x + kCache * kCombineThreads; k < g.nparts; k += kCombineThreads)
+    add((unsigned long long)__double_as_longlong(partial[(long long)k * stride + c]));
   unsigned long long lo = (unsigned long long)acc, hi = (unsigned long long)((unsigned __int128)acc >> 64);
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
@@ -78,8 +92,8 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
   if (threadIdx.x == 0) {
     unsigned __int128 tot = 0;
     for (int w = 0; w < kCombineThreads / 32; ++w) tot += ((unsigned __int128)s_hi[w] << 64) | s_lo[w];
-    const double d = (emax == 0 && tot == 0) ? 0.0 : ldexp(i128_to_double((__int128)tot), E - 1075 - kCombineFrac);
-    out[outidx] = d;
+    // one rounding to f64 with integer operations (the FP64 pipe of this GPU is narrow)
+    out[outidx] = fixed_to_double((__int128)tot, E - 1075 - kCombineFrac);
   }
 }
 
