@@ -264,6 +264,10 @@ def ncu_traffic(name):
 
 
 def run_e2e(args, triot, cfg, xh, yph, ph, dev, stream, step_total):
+    """Steps through the C ABI with every step's inputs copied in from pinned host memory and
+    its results (y, y' and the moment) copied back.  Steps are pipelined over two sets of
+    device buffers: the host-to-device copies of step k+1, the kernels of step k and the
+    device-to-host copies of step k-1 run on three streams at once (the link is full duplex)."""
     import torch
     K = max(3, min(args.steps, args.e2e_steps))
     xp = torch.from_numpy(xh.reshape(cfg.xshape)).pin_memory()
@@ -272,37 +276,56 @@ def run_e2e(args, triot, cfg, xh, yph, ph, dev, stream, step_total):
     y1h = torch.empty(cfg.embed_shape, dtype=torch.float64).pin_memory()
     y2h = torch.empty(cfg.prod_shape, dtype=torch.float64).pin_memory()
     mh = torch.empty(len(cfg.xshape) + 1, dtype=torch.float64).pin_memory()
-    x = torch.empty(cfg.xshape, dtype=torch.float64, device=dev)
-    y1 = torch.empty(cfg.embed_shape, dtype=torch.float64, device=dev)
-    y2 = torch.empty(cfg.prod_shape, dtype=torch.float64, device=dev)
-    p = torch.empty(cfg.xshape, dtype=torch.float64, device=dev)
-    out = torch.empty(len(cfg.xshape) + 1, dtype=torch.float64, device=dev)
-    ws = torch.empty(triot.triot_moment_workspace_size(cfg.xshape, torch.float64) // 8 + 2,
-                     dtype=torch.float64, device=dev)
-
-    def step():
-        x.copy_(xp, non_blocking=True)
-        y2.copy_(yp, non_blocking=True)
-        p.copy_(pp, non_blocking=True)
-        triot.triot_embed(x, y1, stream=stream)
-        triot.triot_product(x, y2, stream=stream)
-        triot.triot_moment(p, out=out, workspace=ws, stream=stream)
-        y1h.copy_(y1, non_blocking=True)
-        y2h.copy_(y2, non_blocking=True)
-        mh.copy_(out, non_blocking=True)
-
+    sets = []
     for _ in range(2):
-        step()
+        sets.append({
+            "x": torch.empty(cfg.xshape, dtype=torch.float64, device=dev),
+            "y1": torch.empty(cfg.embed_shape, dtype=torch.float64, device=dev),
+            "y2": torch.empty(cfg.prod_shape, dtype=torch.float64, device=dev),
+            "p": torch.empty(cfg.xshape, dtype=torch.float64, device=dev),
+            "out": torch.empty(len(cfg.xshape) + 1, dtype=torch.float64, device=dev),
+            "ws": torch.empty(triot.triot_moment_workspace_size(cfg.xshape, torch.float64) // 8 + 2,
+                              dtype=torch.float64, device=dev),
+            "in": torch.cuda.Event(), "done": torch.cuda.Event(), "out_ev": torch.cuda.Event(),
+            "used": False,
+        })
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+
+    def step(k):
+        b = sets[k % 2]
+        with torch.cuda.stream(s_in):
+            if b["used"]:
+                s_in.wait_event(b["out_ev"])   # this set's previous results have left the device
+            b["x"].copy_(xp, non_blocking=True)
+            b["y2"].copy_(yp, non_blocking=True)
+            b["p"].copy_(pp, non_blocking=True)
+            b["in"].record(s_in)
+        s_cmp.wait_event(b["in"])
+        triot.triot_embed(b["x"], b["y1"], stream=s_cmp)
+        triot.triot_product(b["x"], b["y2"], stream=s_cmp)
+        triot.triot_moment(b["p"], out=b["out"], workspace=b["ws"], stream=s_cmp)
+        b["done"].record(s_cmp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(b["done"])
+            y1h.copy_(b["y1"], non_blocking=True)
+            y2h.copy_(b["y2"], non_blocking=True)
+            mh.copy_(b["out"], non_blocking=True)
+            b["out_ev"].record(s_out)
+        b["used"] = True
+
+    for k in range(2):
+        step(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(K):
-        step()
+    for k in range(K):
+        step(k)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     h2d = 8 * (xp.numel() + yp.numel() + pp.numel())
     d2h = 8 * (y1h.numel() + y2h.numel() + mh.numel())
     return {"value": round(step_total * K / dt / 1e9, 1), "unit": "GB/s", "steps": K,
-            "ms_per_step": round(dt / K * 1e3, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "ms_per_step": round(dt / K * 1e3, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "pipelined": "copies in, kernels and copies out of consecutive steps overlap on three streams"}
 
 
 def run_batch(args, triot, synth, dev, stream):
