@@ -9,7 +9,6 @@ namespace triot {
 
 constexpr int kMaxRank = 24;
 constexpr int kMomentWarps = 4;     // warps per CTA of the row-mode moment kernels
-constexpr int kMomentBlkWarps = 2;  // warps per CTA of the block-column moment kernel
 
 // f64 block-column moment: blocks of B elements per staged chunk (the smallest count that
 // covers 16 elements with an even number of elements, so chunks are whole 16-byte pieces)
@@ -107,14 +106,15 @@ struct MomentGeom {
   int D;                           // effective rank
   int m;                           // block mode: the last m axes form blocks of B elements
   int B;                           // (m = 0: row mode, the inner axis alone)
-  int nchunks;                     // chunks per lane segment (the last may be partial)
+  int nchunks;                     // chunks per lane segment (the last may be partial); warp
+                                   // blocks: blocks per staged step
   long long n;                     // elements
   long long seg;                   // lane segment length S (multiple of the chunk)
   long long nwarpseg;              // warp segments (32 lane segments each)
   int n32;                         // n < 2^32: 32-bit decode
   int aligned;                     // p is 16-byte aligned: cp.async staging
-  long long nround;                // f64 block kernel: rounds of 32 chunks (whole tensor)
-  int win;                         // f64 block kernel: rounds per fixed-point window
+  long long nround;                // block kernels: rounds of 32 chunks (warp blocks: blocks)
+  int win;                         // block kernels: rounds (warp blocks: blocks) per window
   FastDiv div[kMaxRank];           // extents (axis order, outermost first)
   long long ext[kMaxRank];         // extents (axis order, outermost first)
 };

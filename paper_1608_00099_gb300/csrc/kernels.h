@@ -17,7 +17,7 @@ const void* moment_kernel_ptr(int dtype, int D, int m = 0, int B = 0);
 const void* moment_blk32_kernel_ptr(int dtype, int B);
 const void* moment_wb_kernel_ptr(int dtype, int B);
 const void* moment_blk64_kernel_ptr(int B, int DO);
-// sticky flag of the f64 block kernel (a bounded wait gave up); reading clears it
+// sticky flags of the block moment kernels (a bounded wait gave up); reading clears them
 void b64_read_device_flag(int* flag);
 void b32_read_device_flag(int* flag);
 void wb_read_device_flag(int* flag);

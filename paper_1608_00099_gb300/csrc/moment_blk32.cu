@@ -33,6 +33,7 @@
 #include "blk32.cuh"
 #include "common.cuh"
 #include "fixed.cuh"
+#include "float_moment.cuh"
 #include "kernels.h"
 
 namespace triot {
@@ -40,33 +41,6 @@ namespace {
 
 // set when a bounded wait for a staged round gives up (read by triot_device_status)
 __device__ int g_b32_flag = 0;
-
-__device__ __forceinline__ void cp16(void* smem, const void* gmem, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
-               : "memory");
-}
-
-// element i (0 .. 16/sizeof(T) - 1) of a 16-byte piece, as f32 (exact for every type)
-template <typename T> struct Piece;
-template <> struct Piece<float> {
-  __device__ static float get(const uint4& v, int i) {
-    const unsigned w = i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-    return __uint_as_float(w);
-  }
-};
-template <> struct Piece<__nv_bfloat16> {
-  __device__ static float get(const uint4& v, int i) {
-    const unsigned w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
-    return __uint_as_float((i & 1) ? (w & 0xFFFF0000u) : (w << 16));
-  }
-};
-template <> struct Piece<__half> {
-  __device__ static float get(const uint4& v, int i) {
-    const unsigned w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
-    return __half2float(__ushort_as_half((unsigned short)((i & 1) ? (w >> 16) : (w & 0xFFFFu))));
-  }
-};
 
 template <typename T, int B>
 __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
@@ -164,11 +138,11 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
         unsigned char* dst = buf + pc * 16 + (pc / H) * PAD;
         const long long off = base + (long long)pc * 16;
         if (full) {
-          cp16(dst, pb + off, 16);
+          fm_cp16(dst, pb + off, 16);
         } else {
           const long long rem = nbytes - off;
           const int nb = rem >= 16 ? 16 : (rem > 0 ? (int)rem : 0);
-          cp16(dst, nb ? (const void*)(pb + off) : (const void*)pb, nb);
+          fm_cp16(dst, nb ? (const void*)(pb + off) : (const void*)pb, nb);
         }
       }
       // the stage's mbarrier also waits for this lane's copies
@@ -193,16 +167,7 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
   // (incomplete) stage is used anyway, so the kernel ends
   unsigned phase = 0;
   auto wait_stage = [&](int q) {
-    const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp][q]);
-    const unsigned par = (phase >> q) & 1u;
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-      asm volatile(
-          "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
-          : "=r"(done)
-          : "r"(bar), "r"(par)
-          : "memory");
-    if (!done && lane == 0) atomicExch(&g_b32_flag, 1);
+    fm_wait((unsigned)__cvta_generic_to_shared(&s_bar[warp][q]), (phase >> q) & 1u, lane, &g_b32_flag);
     phase ^= 1u << q;
   };
 
@@ -297,19 +262,8 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
       jump();
     }
   };
-  // one window sum of every lane into the warp's total (f32 xor tree: a fixed order), kept
-  // as a compensated pair (Knuth's two-sum), so the narrow FP64 pipe is not used per window
-  float* wts = wtot[warp][0];
-  float* wte = wtot[warp][1];
-  auto warp_add = [&](float v, int slot) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) {
-      const float a = wts[slot], t = a + v, bp = t - a;
-      wte[slot] += (a - (t - bp)) + (v - bp);
-      wts[slot] = t;
-    }
-  };
+  // one window sum of every lane into the warp's compensated total
+  auto warp_add = [&](float v, int slot) { fm_warp_add(v, &wtot[warp][0][slot], &wtot[warp][1][slot], lane); };
   // window end: credit every pending mass, move the window's sums into the warp's totals
   auto end_window = [&]() {
     float pend = Q4;
@@ -395,7 +349,7 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
 #pragma unroll
       for (int j = 0; j < B; ++j) {
         const int idx = k * B + j;
-        const float x = Piece<T>::get(v[idx / EPP], idx % EPP);
+        const float x = FPiece<T>::get(v[idx / EPP], idx % EPP);
         cs[j] += x;
         cb[j] = x;
       }
@@ -414,16 +368,7 @@ __global__ void __launch_bounds__(kB32Warps * 32) moment_b32_kernel(
   }
 
   __syncthreads();
-  if (threadIdx.x <= D) {
-    double acc = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      // a non-finite total carries no meaningful compensation (inf - inf there is NaN)
-      const float ts = wtot[w][0][threadIdx.x], te = wtot[w][1][threadIdx.x];
-      acc += isfinite(ts) ? (double)ts + (double)te : (double)ts;
-    }
-    partial[(long long)blockIdx.x * (D + 1) + threadIdx.x] = acc;
-  }
+  if (threadIdx.x <= D) partial[(long long)blockIdx.x * (D + 1) + threadIdx.x] = fm_cta_total<NW>(wtot, threadIdx.x);
 }
 
 template <typename T, int... N>

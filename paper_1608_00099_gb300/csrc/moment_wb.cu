@@ -29,6 +29,7 @@
 #include "blk32.cuh"
 #include "common.cuh"
 #include "fixed.cuh"
+#include "float_moment.cuh"
 #include "kernels.h"
 
 namespace triot {
@@ -36,39 +37,6 @@ namespace {
 
 // set when a bounded wait for a staged step gives up (read by triot_device_status)
 __device__ int g_wb_flag = 0;
-
-__device__ __forceinline__ void wb_cp16(void* smem, const void* gmem, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
-               : "memory");
-}
-
-// element i of a 16-byte piece, and one element of global memory, as f32 (exact)
-template <typename T> struct WbPiece;
-template <> struct WbPiece<float> {
-  __device__ static float get(const uint4& v, int i) {
-    return __uint_as_float(i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w);
-  }
-  __device__ static float ld(const float* p, long long i) { return __ldcs(p + i); }
-};
-template <> struct WbPiece<__nv_bfloat16> {
-  __device__ static float get(const uint4& v, int i) {
-    const unsigned w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
-    return __uint_as_float((i & 1) ? (w & 0xFFFF0000u) : (w << 16));
-  }
-  __device__ static float ld(const __nv_bfloat16* p, long long i) {
-    return __uint_as_float((unsigned)__ldcs(reinterpret_cast<const unsigned short*>(p) + i) << 16);
-  }
-};
-template <> struct WbPiece<__half> {
-  __device__ static float get(const uint4& v, int i) {
-    const unsigned w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
-    return __half2float(__ushort_as_half((unsigned short)((i & 1) ? (w >> 16) : (w & 0xFFFFu))));
-  }
-  __device__ static float ld(const __half* p, long long i) {
-    return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p) + i)));
-  }
-};
 
 // a staged element as f32 (exact for every type)
 __device__ __forceinline__ float wb_elem(const unsigned char* s, float*) {
@@ -157,7 +125,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
       for (long long off = a0 + 16 * lane; off < a1; off += 512) {
         const long long rem = nbytes - off;
         const int nbt = rem >= 16 ? 16 : (rem > 0 ? (int)rem : 0);
-        wb_cp16(buf + (off - a0), nbt ? (const void*)(pb + off) : (const void*)pb, nbt);
+        fm_cp16(buf + (off - a0), nbt ? (const void*)(pb + off) : (const void*)pb, nbt);
       }
       asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
     } else {
@@ -176,16 +144,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
   // (incomplete) stage is used anyway, so the kernel ends
   unsigned phase = 0;
   auto wait_stage = [&](int q) {
-    const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp][q]);
-    const unsigned par = (phase >> q) & 1u;
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-      asm volatile(
-          "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
-          : "=r"(done)
-          : "r"(bar), "r"(par)
-          : "memory");
-    if (!done && lane == 0) atomicExch(&g_wb_flag, 1);
+    fm_wait((unsigned)__cvta_generic_to_shared(&s_bar[warp][q]), (phase >> q) & 1u, lane, &g_wb_flag);
     phase ^= 1u << q;
   };
 
@@ -230,18 +189,8 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
   };
   // block column of this lane's column slot r
   auto col = [&](int r) { return VEC ? (lane + 32 * (r / EPV)) * EPV + r % EPV : lane + 32 * r; };
-  // one window sum of every lane into the warp's total (f32 xor tree: a fixed order)
-  float* wts = wtot[warp][0];
-  float* wte = wtot[warp][1];
-  auto warp_add = [&](float v, int slot) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) {
-      const float a = wts[slot], t = a + v, bp = t - a;
-      wte[slot] += (a - (t - bp)) + (v - bp);
-      wts[slot] = t;
-    }
-  };
+  // one window sum of every lane into the warp's compensated total
+  auto warp_add = [&](float v, int slot) { fm_warp_add(v, &wtot[warp][0][slot], &wtot[warp][1][slot], lane); };
   // window end: credit every pending mass, move the window's sums into the warp's totals
   auto end_window = [&]() {
     float pend = Q3;
@@ -345,7 +294,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
         if (q + u >= q1) break;
         float x[C];
 #pragma unroll
-        for (int r = 0; r < C; ++r) x[r] = WbPiece<T>::get(xv[u][r / EPV], r % EPV);
+        for (int r = 0; r < C; ++r) x[r] = FPiece<T>::get(xv[u][r / EPV], r % EPV);
         do_block(x);
       }
     }
@@ -354,7 +303,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
     for (long long q = q0; q < q1; ++q) {
       float x[C];
 #pragma unroll
-      for (int r = 0; r < C; ++r) x[r] = WbPiece<T>::ld(p, q * B + col(r));
+      for (int r = 0; r < C; ++r) x[r] = FPiece<T>::ld(p, q * B + col(r));
       do_block(x);
     }
   } else {
@@ -386,16 +335,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
   if (wpos > 0) end_window();
 
   __syncthreads();
-  if (threadIdx.x <= D) {
-    double acc = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      // a non-finite total carries no meaningful compensation (inf - inf there is NaN)
-      const float ts = wtot[w][0][threadIdx.x], te = wtot[w][1][threadIdx.x];
-      acc += isfinite(ts) ? (double)ts + (double)te : (double)ts;
-    }
-    partial[(long long)blockIdx.x * (D + 1) + threadIdx.x] = acc;
-  }
+  if (threadIdx.x <= D) partial[(long long)blockIdx.x * (D + 1) + threadIdx.x] = fm_cta_total<NW>(wtot, threadIdx.x);
 }
 
 template <typename T, int... N>

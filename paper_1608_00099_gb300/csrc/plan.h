@@ -46,7 +46,7 @@ struct MomentLaunch {
   CombineGeom cg;
   int grid = 0;        // CTAs of the moment kernel (= number of partial vectors)
   int warps = 4;       // warps per CTA
-  size_t smem = 0;     // dynamic shared memory per CTA (f64 block kernel: outer-axis state)
+  size_t smem = 0;     // dynamic shared memory per CTA (block kernels: stages, outer-axis state)
   bool empty = false;  // nothing to sum: only the combine runs (it writes zeros)
 };
 // `occ` = resident CTAs per SM of the chosen kernel (from the occupancy calculator).
