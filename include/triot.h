@@ -170,10 +170,14 @@ int triot_moment_workspace_size(int rank, const int64_t* shape, int dtype, size_
  *   aligned, owned by the caller; its contents on entry are ignored.
  *   Accumulation: f64 input in two's-complement fixed point, exact within windows of at
  *   most 1024 elements per thread and rounded to f64 once per window (error at most
- *   2^-52 times the window's largest |p| per element); f32/bf16/f16 input in compensated
- *   f32 per thread.  Block partials are combined by a second kernel in fixed point,
- *   independent of their order, so results are bit-identical from run to run.  Two
- *   kernels are enqueued on `stream`.
+ *   2^-52 times the window's largest |p| per element).  f32/bf16/f16 input in f32: with
+ *   compensated sums per thread when the innermost extent exceeds 16, otherwise (trailing
+ *   axes forming blocks) with plain f32 sums of at most 64 terms per thread and window,
+ *   added across each warp into compensated f32 totals (error below about 5.6e-6 of
+ *   sum |p[t]| t_i); finite f32 data whose partial sums exceed the f32 range give inf.
+ *   Block partials are combined by a second kernel in fixed point, independent of their
+ *   order, so results are bit-identical from run to run.  Two kernels are enqueued on
+ *   `stream`.
  */
 int triot_moment(int rank, const int64_t* shape, const void* p, int dtype, double* out,
                  void* workspace, size_t workspace_bytes, void* stream);
