@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "blk32.cuh"
@@ -249,9 +250,11 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
     }
   }
 
-  // one block: the lane's C column values (in slot order)
+  // one block: the lane's C column values (in slot order); `win` = check for the window end
+  // here (the vector path checks once per group of blocks, so the window end has a single
+  // call site in its loop)
   int wpos = 0;
-  auto do_block = [&](const float (&x)[C]) {
+  auto do_block = [&](const float (&x)[C], auto win) {
     float part = 0.f;
 #pragma unroll
     for (int r = 0; r < C; ++r) {
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
         cold_carry();
       }
     }
-    if (++wpos == kWBTerms) {
+    if (decltype(win)::value && ++wpos == kWBTerms) {
       end_window();
       wpos = 0;
     }
@@ -280,6 +283,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
     // loads in flight
     constexpr int CV = VEC ? C / EPV : 1;
     constexpr int UV = 8 / CV;
+    static_assert(kWBTerms % UV == 0, "a window is a whole number of vector steps");
     const uint4* pv = reinterpret_cast<const uint4*>(p);
     const long long bv = B / EPV;  // vectors per block
     for (long long q = q0; q < q1; q += UV) {
@@ -295,7 +299,13 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
         float x[C];
 #pragma unroll
         for (int r = 0; r < C; ++r) x[r] = FPiece<T>::get(xv[u][r / EPV], r % EPV);
-        do_block(x);
+        do_block(x, std::false_type{});
+      }
+      // UV divides kWBTerms, so a window holds exactly kWBTerms blocks
+      wpos += UV;
+      if (wpos == kWBTerms) {
+        end_window();
+        wpos = 0;
       }
     }
   } else if (VEC) {
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
       float x[C];
 #pragma unroll
       for (int r = 0; r < C; ++r) x[r] = FPiece<T>::ld(p, q * B + col(r));
-      do_block(x);
+      do_block(x, std::true_type{});
     }
   } else {
     long long si = 0;  // next step to stage
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
 #pragma unroll
         for (int r = 0; r < C; ++r)
           x[r] = (r < C - 1 || lane + 32 * r < B) ? wb_elem(bl + 32 * r * ES, (T*)nullptr) : 0.f;
-        do_block(x);
+        do_block(x, std::true_type{});
       }
       if (++buf == NS) buf = 0;
       __syncwarp();
