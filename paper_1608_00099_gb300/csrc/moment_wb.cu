@@ -279,20 +279,22 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
   };
 
   if (VEC && g.aligned) {
-    // direct 16-byte loads: lane l holds vectors l, l + 32, .. of each block, UV blocks'
-    // loads in flight
+    // direct 16-byte loads: lane l holds vectors l, l + 32, .. of each block; groups of UV
+    // blocks, the next group's loads issued before the current group is summed
     constexpr int CV = VEC ? C / EPV : 1;
     constexpr int UV = 8 / CV;
     static_assert(kWBTerms % UV == 0, "a window is a whole number of vector steps");
     const uint4* pv = reinterpret_cast<const uint4*>(p);
     const long long bv = B / EPV;  // vectors per block
-    for (long long q = q0; q < q1; q += UV) {
-      uint4 xv[UV][CV];
+    // group of UV blocks from block q into registers (blocks past q1 read as zeros)
+    auto load = [&](uint4 (&xv)[UV][CV], long long q) {
 #pragma unroll
       for (int u = 0; u < UV; ++u)
 #pragma unroll
         for (int v = 0; v < CV; ++v)
           xv[u][v] = (q + u < q1) ? __ldcs(pv + (q + u) * bv + lane + 32 * v) : make_uint4(0u, 0u, 0u, 0u);
+    };
+    auto process = [&](const uint4 (&xv)[UV][CV], long long q) {
 #pragma unroll
       for (int u = 0; u < UV; ++u) {
         if (q + u >= q1) break;
@@ -307,6 +309,16 @@ __global__ void __launch_bounds__(kWBWarps * 32, 4) moment_wb_kernel(
         end_window();
         wpos = 0;
       }
+    };
+    // two register buffers: the next group's loads are in flight while a group is summed
+    uint4 xa[UV][CV], xb[UV][CV];
+    if (q0 < q1) load(xa, q0);
+    for (long long q = q0; q < q1; q += 2 * UV) {
+      if (q + UV < q1) load(xb, q + UV);
+      process(xa, q);
+      if (q + UV >= q1) break;
+      if (q + 2 * UV < q1) load(xa, q + 2 * UV);
+      process(xb, q + UV);
     }
   } else if (VEC) {
     // unaligned base: element loads at the same columns
