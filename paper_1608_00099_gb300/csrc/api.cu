@@ -47,7 +47,7 @@ int device_info(DeviceInfo& out) {
   cudaDeviceProp prop;
   e = cudaGetDeviceProperties(&prop, dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
-  snprintf(d.name, sizeof d.name, "%s", prop.name);
+  snprintf(d.name, sizeof d.name, "%.*s", (int)sizeof d.name - 1, prop.name);
   cache.push_back(d);
   out = d;
   return TRIOT_OK;
