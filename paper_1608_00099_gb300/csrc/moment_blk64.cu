@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
   if (threadIdx.x == 32) {
     // a lane's next block after its chunk is 32K - K + 1 blocks on; the outermost axis keeps
     // the remainder (it never wraps inside the tensor)
-    unsigned long long J = 32ull * K - (K - 1);
+    uint32_t J = 32u * K - (K - 1);  // below 2^32: magic-number division (Alg 4)
     for (int a = DO - 1; a >= 1; --a) {
-      const unsigned long long e = (unsigned long long)g.ext[a];
-      s_jd[a] = (uint32_t)(J % e);
-      J /= e;
+      const uint32_t q = fdiv(J, g.div[a]);
+      s_jd[a] = J - q * g.div[a].d;
+      J = q;
     }
-    if (DO >= 1) s_jd[0] = (uint32_t)J;
+    if (DO >= 1) s_jd[0] = J;
   }
   if ((threadIdx.x & 31) == 0) {
     for (int q = 0; q < NS; ++q) {
