@@ -58,6 +58,7 @@ BLOCK_SHAPES = [
     (3,) * 12, (100003, 10), (31, 37, 41, 8), (3, 5, 7, 4), (2, 3, 1, 5, 1, 3), (61, 67, 11),
     (1, 1, 12), (8191, 1, 1), (999, 15), (3001, 13), (77, 7), (40, 2, 7), (1, 1, 1),
     (7, 2, 128), (3, 5, 256), (1001, 33), (70, 4, 64), (6, 4, 7, 3, 5, 3, 3, 3, 6, 3),
+    (16, 16), (2, 128), (9, 15),                # one block: no outer axis
 ]
 
 
