@@ -432,6 +432,16 @@ def run_extra_workloads(args, triot, synth, dev, stream):
     x2 = [torch.empty_like(xs[0]) for _ in range(ncopy)]
     ms = time_op(lambda k, st: triot.triot_crop(x2[k % ncopy], ys[k % ncopy], stream=st), 4 * ncopy, stream)
     res["embed_f64_d6"]["crop"] = op_entry(2 * 8 * int(np.prod(cfg.xshape)), ms, peak)
+    # single-launch latency: events around one plain call (host launch path included), median
+    lat = []
+    for k in range(21):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        triot.triot_embed(xs[k % ncopy], ys[k % ncopy], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1) * 1e3)
+    res["embed_f64_d6"]["single_launch_us"] = round(sorted(lat)[len(lat) // 2], 2)
     del xs, ys, x2
     # f32 d=24: 44 GB embed target, product over the all-2 intersection, moment of x
     cfg = synth.config_f32_d24()
