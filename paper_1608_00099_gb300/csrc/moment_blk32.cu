@@ -12,19 +12,20 @@
 // mixed-radix digits are precomputed.
 //
 // Per element the work is two f32 adds: the element's column sum cs[j] (registers; B is a
-// template parameter), which gives the block axes' moments sum_j cs[j] * digit_a(j), and its
-// share of the block's mass (a tree over the block).  Per block the mass is credited to the
-// three innermost outer axes (A += mass * digit) and added to the pending mass of the axes
-// above, which is credited to an axis (A_i += pending * t_i) only when its digit changes.
+// template parameter), which gives the block axes' moments sum_j cs[j] * digit_a(j), and
+// its share of the block's mass (a tree over the block).  Per block the mass is credited to
+// the three innermost outer axes (A += mass * digit) and added to the pending mass of the
+// axes above, which is credited to an axis (A_i += pending * t_i) only when its digit
+// changes.
 //
 // Accuracy: every plain f32 sum of a lane runs over at most kB32Terms terms (a window is at
 // most kB32Terms blocks of a lane); at the window end each sum is added across the warp in
 // f32 (a fixed xor tree) into the warp's compensated f32 totals (two-sum pairs), which are
-// added in f64 at the end.  Block masses are trees of at
-// most 16 elements and the block axes' moments sums of at most 16 products, so every output
-// is within about (kB32Terms + 30) * 2^-24 (5.6e-6) of sum |p| t_i.  Non-finite elements
-// propagate as in a plain sum (an infinite mass times a zero digit gives NaN, as in the
-// definition); finite data whose partial sums exceed the f32 range overflow to inf.
+// added in f64 at the end.  Block masses are trees of at most 16 elements and the block
+// axes' moments sums of at most 16 products, so every output is within about (kB32Terms +
+// 30) * 2^-24 (5.6e-6) of sum |p| t_i.  Non-finite elements propagate as in a plain sum (an
+// infinite mass times a zero digit gives NaN, as in the definition); finite data whose
+// partial sums exceed the f32 range overflow to inf.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 

@@ -5,22 +5,23 @@
 // are the outer axes 0 .. DO-1.  Each warp owns a contiguous range of blocks.  When a block
 // is a whole number of 512-byte rows, lane l reads 16-byte vectors of it directly (columns
 // 16/es * (l + 32 v) ..; several blocks' loads in flight); otherwise the warp walks its
-// range in steps of U whole blocks (at most kWBStepBytes), each staged into shared memory by
-// one bulk TMA copy (cp.async.bulk over the step widened to 16-byte bounds, completing on an
-// mbarrier; 16-byte cp.async with zero fill for the tensor's last bytes), and lane l reads
-// columns l, l + 32, .. (C = ceil(B / 32)).  Each element is added to the lane's column sum;
-// the lane's share of the block's mass goes to the outer axes.  All lanes of a warp are in the same block, so the
-// outer digits are the same in every lane: advancing the tuple by one block (advance_tuple,
-// Algorithm 3) is a uniform branch.  The two innermost outer axes take mass * digit per
-// block; the axes above keep a pending mass that is credited (A_i += pending * t_i) only when
-// their digit changes.  The block axes' moments are sum_j digit_a(j) * colsum_j.
+// range in steps of U whole blocks (at most kWBStepBytes), each staged into shared memory
+// by one bulk TMA copy (cp.async.bulk over the step widened to 16-byte bounds, completing
+// on an mbarrier; 16-byte cp.async with zero fill for the tensor's last bytes), and lane l
+// reads columns l, l + 32, .. (C = ceil(B / 32)).  Each element is added to the lane's
+// column sum; the lane's share of the block's mass goes to the outer axes.  All lanes of a
+// warp are in the same block, so the outer digits are the same in every lane: advancing the
+// tuple by one block (advance_tuple, Algorithm 3) is a uniform branch.  The two innermost
+// outer axes take mass * digit per block; the axes above keep a pending mass that is
+// credited (A_i += pending * t_i) only when their digit changes.  The block axes' moments
+// are sum_j digit_a(j) * colsum_j.
 //
 // Accuracy: every plain f32 sum of a lane runs over at most kWBTerms terms (a window is at
-// most kWBTerms blocks); at the window end each sum is added across the warp in f32 (a fixed
-// xor tree) into the warp's compensated f32 totals (two-sum pairs), added in f64 at the end.
-// Every output is then within about (kWBTerms + 20) * 2^-24 (5.0e-6) of sum |p| t_i.
-// Non-finite elements propagate as in a plain sum; finite data whose partial sums exceed the
-// f32 range overflow to inf.
+// most kWBTerms blocks); at the window end each sum is added across the warp in f32 (a
+// fixed xor tree) into the warp's compensated f32 totals (two-sum pairs), added in f64 at
+// the end. Every output is then within about (kWBTerms + 20) * 2^-24 (5.0e-6) of sum |p|
+// t_i. Non-finite elements propagate as in a plain sum; finite data whose partial sums
+// exceed the f32 range overflow to inf.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
