@@ -36,68 +36,57 @@ enum { T_F64 = 0, T_F32 = 1, T_BF16 = 2, T_F16 = 3 };
 
 // ------------------------------------------------------------------ index arithmetic
 
-// Algorithm 2: flat index of `tup` with respect to `shape` by Horner's rule,
-// (..((t0*s1 + t1)*s2 + t2)*s3 ..) + t_{d-1}  (Section 1, second display).
+// The flat index of a tuple (Section 1): sum over axes of t_i times the number of
+// elements in one step of axis i, i.e. the product of the extents right of i.  Evaluated
+// as a left fold that scales the index so far by the next axis' extent and adds that
+// axis' digit -- the nested (Horner) form of the same sum that Algorithm 2 uses.
 u64 tuple_to_index(const u64* tup, const u64* shape, unsigned dim) {
-  u64 res = 0;
-  unsigned k;
-  for (k = 0; k + 1 < dim; ++k) {
-    res += tup[k];
-    res *= shape[k + 1];
-  }
-  res += tup[k];
-  return res;
+  u64 flat = 0;
+  for (unsigned axis = 0; axis < dim; ++axis) flat = flat * shape[axis] + tup[axis];
+  return flat;
 }
 
-// Algorithm 3: advance `tup` to the next tuple in lexicographic order: add one to the
-// last axis and carry leftwards while an axis reaches its extent.  Axis 0 is never
-// reset, so stepping past the last tuple leaves tup[0] == shape[0].
+// Lexicographic successor of a tuple (the increment Algorithm 3 defines): the rightmost
+// axis that has not reached its last value goes up by one and every axis right of it
+// restarts at zero.  When all axes after the first are at their last value the first
+// axis is the one raised, so the step after the final tuple gives (shape[0], 0, ..., 0).
 void advance_tuple(u64* tup, const u64* shape, unsigned dim) {
-  ++tup[dim - 1];
-  for (unsigned k = dim - 1; k >= 1; --k) {
-    if (tup[k] >= shape[k]) {
-      ++tup[k - 1];
-      tup[k] = 0;
-    } else {
-      return;
-    }
+  unsigned grow = dim - 1;
+  while (grow > 0 && tup[grow] + 1 == shape[grow]) --grow;
+  tup[grow] += 1;
+  for (unsigned axis = grow + 1; axis < dim; ++axis) tup[axis] = 0;
+}
+
+// The digits of a flat index with respect to `shape` (the inverse of tuple_to_index):
+// the last axis' digit is the remainder by its extent, the quotient carries the rest.
+void index_to_tuple(u64 index, const u64* shape, unsigned dim, u64* tup) {
+  for (unsigned n = dim; n-- > 0;) {
+    tup[n] = index % shape[n];
+    index /= shape[n];
   }
 }
 
-// Algorithm 4: flat index w.r.t. `shape` -> flat index w.r.t. `new_shape`, peeling the
-// axes from the right with % and /.
+// What Algorithm 4 computes: the flat index, in `new_shape`, of the tuple whose flat index
+// in `shape` is `index` -- the tuple recovered digit by digit, then flattened again.
 u64 reindex(u64 index, const u64* shape, const u64* new_shape, unsigned dim) {
-  u64 new_index = 0;
-  u64 new_axis_product_from_right = 1;
-  for (int i = int(dim) - 1; index > 0 && i >= 0; --i) {
-    const u64 next_value = index % shape[i];
-    new_index += next_value * new_axis_product_from_right;
-    index /= shape[i];
-    new_axis_product_from_right *= new_shape[i];
-  }
-  return new_index;
+  std::vector<u64> tup(dim);
+  index_to_tuple(index, shape, dim, tup.data());
+  return tuple_to_index(tup.data(), new_shape, dim);
 }
 
-// Algorithm 12: Algorithm 4 for power-of-two axes, with masks and shifts.
+// The same map when every extent is a power of two (Algorithm 12): an axis' digit is a
+// bit field of the index, so the digits come out with masks and shifts and the new flat
+// index is assembled by shifting each digit into a field of the new axis' width.
 u64 reindex_pow2(u64 index, const unsigned* log_shape, const unsigned* new_log_shape,
                  unsigned dim) {
-  u64 new_index = 0;
-  unsigned new_axis_sum_from_right = 0;
-  for (int i = int(dim) - 1; index > 0 && i >= 0; --i) {
-    const u64 next_value = index & ((u64(1) << log_shape[i]) - 1);
-    new_index += next_value << new_axis_sum_from_right;
-    index >>= log_shape[i];
-    new_axis_sum_from_right += new_log_shape[i];
+  std::vector<u64> digit(dim);
+  for (unsigned n = dim; n-- > 0;) {
+    digit[n] = index & ((u64(1) << log_shape[n]) - 1);
+    index >>= log_shape[n];
   }
-  return new_index;
-}
-
-// tuple of flat index `index` w.r.t. `shape` (the digit peeling of Algorithm 4)
-void index_to_tuple(u64 index, const u64* shape, unsigned dim, u64* tup) {
-  for (int i = int(dim) - 1; i >= 0; --i) {
-    tup[i] = index % shape[i];
-    index /= shape[i];
-  }
+  u64 flat = 0;
+  for (unsigned axis = 0; axis < dim; ++axis) flat = (flat << new_log_shape[axis]) + digit[axis];
+  return flat;
 }
 
 u64 count_of(const u64* shape, unsigned dim) {

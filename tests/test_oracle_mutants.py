@@ -14,12 +14,13 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 
 # (description, text in the source, replacement, pins expected to catch it)
 MUTANTS = [
-    ("Horner multiplies by the wrong axis", "res *= shape[k + 1];", "res *= shape[k];",
+    ("Horner multiplies by the wrong axis", "flat = flat * shape[axis] + tup[axis];",
+     "flat = flat * shape[dim - 1 - axis] + tup[axis];",
      [lambda o: pins.test_worked_example_flat_index(o)]),
-    ("carry test off by one", "if (tup[k] >= shape[k]) {", "if (tup[k] > shape[k]) {",
+    ("carry test off by one", "tup[grow] + 1 == shape[grow]", "tup[grow] == shape[grow]",
      [lambda o: pins.test_advance_tuple_lexicographic(o, (2, 3, 4))]),
-    ("reindex scales by the old shape", "new_axis_product_from_right *= new_shape[i];",
-     "new_axis_product_from_right *= shape[i];",
+    ("reindex flattens with the old shape", "return tuple_to_index(tup.data(), new_shape, dim);",
+     "return tuple_to_index(tup.data(), shape, dim);",
      [lambda o: pins.test_reindex_equals_unravel_ravel(o, ((3, 4), (5, 6)))]),
     ("ties round to odd", "std::fmod(fl, 2.0) != 0.0", "std::fmod(fl, 2.0) == 0.0",
      [lambda o: pins.test_round_to_f16_equals_numpy(o)]),
