@@ -338,6 +338,9 @@ def run_batch(args, triot, synth, dev, stream):
     outs = [torch.zeros(len(pr.xshape) + 1, dtype=torch.float64, device=dev) for pr in pairs]
     ny = sum(int(np.prod(pr.yshape)) for pr in pairs)
     nx = sum(int(np.prod(pr.xshape)) for pr in pairs)
+    # launch geometry of each mode chosen by measurement (cached; the plans pick it up)
+    tuned = {"fused": triot.triot_batch_autotune(xs, ys, outs, mode=triot.BATCH_FUSED, stream=stream),
+             "phased": triot.triot_batch_autotune(xs, ys, outs, mode=triot.BATCH_PHASED, stream=stream)}
     fused = triot.BatchPlan(xs, ys, outs, mode=triot.BATCH_FUSED)
     phased = triot.BatchPlan(xs, ys, outs, mode=triot.BATCH_PHASED)
 
@@ -372,7 +375,11 @@ def run_batch(args, triot, synth, dev, stream):
                      ("plain_in_graph", ms_pg)):
         res[name] = {"ms": round(ms, 3), "elem_per_s": round(ny / (ms * 1e-3), 1),
                      "gbs_fused_bytes": round(fused_bytes / (ms * 1e-3) / 1e9, 1)}
-    res["launches"] = {"fused_graph": 2, "phased_graph": 4, "plain_launches": 4 * len(pairs)}
+    # kernels per run: fill, x-driven fused pass, combine / fill, embed, product, moment,
+    # combine / per pair embed, product, moment, moment combine
+    res["launches"] = {"fused_graph": 3, "phased_graph": 5, "plain_launches": 4 * len(pairs)}
+    res["tuning"] = {"autotuned": tuned, "geometry_fused": fused.geometry(),
+                     "geometry_phased": phased.geometry()}
     res["speedup_fused_vs_plain"] = round(ms_plain / ms_f, 2)
     fused.close()
     phased.close()

@@ -194,9 +194,14 @@ int triot_moment(int rank, const int64_t* shape, const void* p, int dtype, doubl
  *   allocates nothing (no cudaMalloc, no library allocator).
  *   Arguments as triot_moment without the workspace.  Fails with TRIOT_ERR_WORKSPACE,
  *   and enqueues nothing, when the launch would need more partials than the scratch
- *   holds (rare: the partials number grid * (effective rank + 1), grid about SMs * 4).
+ *   holds: the partials number grid * (effective rank + 1), where the grid is at most
+ *   SMs x resident CTAs per SM of the chosen moment kernel (or x the tuned ctas_per_sm);
+ *   the default plans of every workload this library measures fit (for example 9^8 in f64
+ *   and 2^24 elements of rank 24 in f32), a forced ctas_per_sm of 32 at rank 24 does not.
  *   The first call on a device looks up the scratch's device address (once, with that
- *   device current); make that first call before any stream capture.  All calls share the
+ *   device current) and keeps it for the life of the process: make that first call before
+ *   any stream capture, and do not use this call across a cudaDeviceReset (the address it
+ *   keeps belongs to the context the reset destroys).  All calls share the
  *   one scratch array, which keeps the last call's contents: calls whose kernels may
  *   overlap on the GPU (different streams without ordering) race on it.
  */
@@ -272,9 +277,13 @@ typedef struct triot_plan triot_plan;
  * triot_batch_plan_create -- validate `n` descriptors (all of one dtype: TRIOT_F32,
  *   TRIOT_F64, TRIOT_BF16 or TRIOT_F16), build the device work list (descriptors, tile
  *   prefix sums, moment slots) and return an opaque plan.  This call allocates device
- *   memory (once); running the plan does not.  `tune` may be NULL.  Rejects descriptors
- *   whose x is not inside y, ranks out of range or NULL pointers (TRIOT_ERR_*; nothing
- *   is allocated then).
+ *   memory (once); running the plan does not.  Geometry: tile_elems (elements of a work
+ *   tile, 1 .. 2^20) and ctas_per_sm (1 .. 32) come from `tune` where non-zero, else from
+ *   the tuning cache entry for this batch (TRIOT_OP_BATCH, keyed by GPU, dtype, mode and
+ *   the size classes floor(log2 n) and floor(log2 sum |y|); see triot_batch_autotune),
+ *   else 1024 and 4; `tune` may be NULL.  Rejects descriptors whose x is not inside y,
+ *   ranks out of range, NULL pointers or out-of-range tuning values (TRIOT_ERR_*;
+ *   nothing is allocated then).
  */
 int triot_batch_plan_create(const triot_batch_desc* descs, int n, int dtype, int mode,
                             const triot_tune* tune, triot_plan** out);
@@ -289,6 +298,21 @@ int triot_batch_run_plain(triot_plan* plan, void* stream);
 /* Bytes of device memory the plan holds, and its tile count. */
 int triot_batch_plan_info(const triot_plan* plan, size_t* device_bytes, int64_t* tiles);
 int triot_batch_plan_destroy(triot_plan* plan);
+/* The geometry a plan runs with (threads per CTA, tile_elems, ctas_per_sm). */
+int triot_batch_plan_geometry(const triot_plan* plan, triot_tune* out);
+/*
+ * triot_batch_autotune -- the batch's launch geometry chosen by measurement: for every
+ *   candidate (tile_elems in {256, 512, 1024, 2048, 4096} x ctas_per_sm in {2, 4, 8}) a
+ *   plan is built, run twice, then timed over three graph launches with CUDA events on
+ *   `stream`; the fastest (median) is stored in the tuning cache under this batch's key
+ *   (so that later triot_batch_plan_create calls with a NULL or zero `tune` use it, and
+ *   triot_tune_save persists it) and returned in *best (may be NULL).  Runs the whole
+ *   pipeline on the caller's buffers (each run rewrites every y and moment output the
+ *   same way), allocates and frees candidate plans, and synchronises `stream`.  Errors as
+ *   triot_batch_plan_create, or TRIOT_ERR_CUDA.
+ */
+int triot_batch_autotune(const triot_batch_desc* descs, int n, int dtype, int mode, void* stream,
+                         triot_tune* best);
 
 /* ------------------------------------------------------------------ tuning */
 
@@ -297,7 +321,7 @@ int triot_batch_plan_destroy(triot_plan* plan);
 #define TRIOT_OP_CROP 1
 #define TRIOT_OP_PRODUCT 2
 #define TRIOT_OP_MOMENT 3
-#define TRIOT_OP_BATCH 4
+#define TRIOT_OP_BATCH 4   /* batches: see triot_batch_autotune */
 
 /*
  * triot_autotune -- time candidate launch geometries for one (op, rank, shapes, dtype)
@@ -352,8 +376,20 @@ int triot_canonicalize(int op, int rank, const int64_t* xshape, const int64_t* y
 int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q, uint32_t* r);
 
 /* Sticky device-side status (TRIOT_OK or TRIOT_ERR_DEVICE) of the current device; reading
- * it synchronises the device and clears it. */
+ * it synchronises the device and clears it.  It is set when a kernel's bounded wait for a
+ * staged copy gave up (the kernel then finishes with what it has, so its results are not
+ * to be trusted) or when a batch work list holds a corrupted pair index. */
 int triot_device_status(void);
+
+/*
+ * triot_selftest_wait_timeout -- a test of the failure path above, with nothing at risk:
+ *   one warp waits on an mbarrier that expects an arrival nobody makes and that no copy
+ *   targets, polling it `limit` times (1 .. 4096) with the same bounded wait the moment
+ *   kernels use for their staged copies; the wait runs out, the kernel records it and
+ *   returns.  The next triot_device_status() then returns TRIOT_ERR_DEVICE (and clears the
+ *   flag); the context stays usable.  Not part of the paper's method.
+ */
+int triot_selftest_wait_timeout(int limit, void* stream);
 
 #ifdef __cplusplus
 }

@@ -303,12 +303,14 @@ int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q
 int triot_device_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-  int flag = 0, flag2 = 0, flag3 = 0, flag4 = 0;
+  int flag = 0, flag2 = 0, flag3 = 0, flag4 = 0, flag5 = 0;
   st_read_device_flag(&flag);
   b64_read_device_flag(&flag2);
   b32_read_device_flag(&flag3);
   wb_read_device_flag(&flag4);
-  return (flag || flag2 || flag3 || flag4) ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped") : ok();
+  selftest_read_device_flag(&flag5);
+  return (flag || flag2 || flag3 || flag4 || flag5) ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped")
+                                                    : ok();
 }
 
 }  // extern "C"

@@ -556,6 +556,7 @@ struct triot_plan_impl {
   void* d_ws = nullptr;                    // moment workspace of the plain launches
   size_t ws_bytes = 0;
   size_t dev_bytes = 0;
+  int tile_elems = 0, ctas_per_sm = 0;     // geometry in force
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
 };
@@ -686,17 +687,11 @@ int triot_batch_plan_create(const triot_batch_desc* descs, int n, int dtype, int
   if (!descs || n <= 0) return fail(TRIOT_ERR_ARG, "need at least one descriptor");
   if (!valid_dtype(dtype)) return fail(TRIOT_ERR_DTYPE, "unknown dtype code");
   if (mode != TRIOT_BATCH_FUSED && mode != TRIOT_BATCH_PHASED) return fail(TRIOT_ERR_ARG, "unknown batch mode");
+  if (tune && (tune->tile_elems < 0 || tune->tile_elems > (1 << 20) || tune->ctas_per_sm < 0 ||
+               tune->ctas_per_sm > 32))
+    return fail(TRIOT_ERR_ARG, "tile_elems or ctas_per_sm out of range");
   const int es = dtype_size(dtype);
-  DeviceInfo dev;
-  int st = device_info(dev);
-  if (st) return st;
-  const long long target = (tune && tune->tile_elems > 0) ? tune->tile_elems : 1024;
-  if (target < 1) return fail(TRIOT_ERR_ARG, "tile_elems out of range");
-  std::vector<PairDev> host(n);
-  std::vector<int> tile_pair, xtile_pair, fill_pair;
-  int maxrank = 1;
-  long long ntiles = 0, nxtiles = 0, nfill = 0;
-  size_t max_ws = 16;
+  // every descriptor is checked before anything touches the GPU
   for (int i = 0; i < n; ++i) {
     const triot_batch_desc& d = descs[i];
     char buf[160];
@@ -710,6 +705,10 @@ int triot_batch_plan_create(const triot_batch_desc* descs, int n, int dtype, int
         snprintf(buf, sizeof buf, "descriptor %d: axis %d needs 1 <= x extent <= y extent < 2^31", i, a);
         return fail(TRIOT_ERR_SHAPE, buf);
       }
+      if (ny > (1ll << 40) / d.yshape[a]) {
+        snprintf(buf, sizeof buf, "descriptor %d: more than 2^40 elements", i);
+        return fail(TRIOT_ERR_SHAPE, buf);
+      }
       ny *= d.yshape[a];
       nx *= d.xshape[a];
     }
@@ -720,6 +719,36 @@ int triot_batch_plan_create(const triot_batch_desc* descs, int n, int dtype, int
     if (overlaps_bytes(d.x, size_t(nx) * es, d.y, size_t(ny) * es)) {
       snprintf(buf, sizeof buf, "descriptor %d: x and y overlap", i);
       return fail(TRIOT_ERR_ALIAS, buf);
+    }
+  }
+  DeviceInfo dev;
+  int st = device_info(dev);
+  if (st) return st;
+  // geometry: the caller's values, else the tuned ones for this batch's key, else defaults
+  TuneCfg tuned;
+  {
+    long long ny_total = 0;
+    for (int i = 0; i < n; ++i) {
+      long long ny = 1;
+      for (int a = 0; a < descs[i].rank; ++a) ny *= descs[i].yshape[a];
+      ny_total += ny;
+    }
+    tuned = tune_lookup_key(batch_key(dtype, mode, n, ny_total));
+  }
+  const long long target = (tune && tune->tile_elems > 0) ? tune->tile_elems
+                           : tuned.tile_elems > 0           ? tuned.tile_elems
+                                                            : 1024;
+  std::vector<PairDev> host(n);
+  std::vector<int> tile_pair, xtile_pair, fill_pair;
+  int maxrank = 1;
+  long long ntiles = 0, nxtiles = 0, nfill = 0;
+  size_t max_ws = 16;
+  for (int i = 0; i < n; ++i) {
+    const triot_batch_desc& d = descs[i];
+    long long ny = 1, nx = 1;
+    for (int a = 0; a < d.rank; ++a) {
+      ny *= d.yshape[a];
+      nx *= d.xshape[a];
     }
     const long long rows = ny / d.yshape[d.rank - 1];
     if (rows > 0xFFFFFFFFll) return fail(TRIOT_ERR_SHAPE, "a pair has more than 2^32 rows");
@@ -787,7 +816,7 @@ int triot_batch_plan_create(const triot_batch_desc* descs, int n, int dtype, int
         ys *= d.yshape[a];
       }
     }
-    const long long xtarget = 1024;
+    const long long xtarget = target;
     if (p.xinner <= xtarget) {
       long long R = std::max(1ll, std::min(256ll, xtarget / p.xinner));
       R = std::min(R, p.xrows);
@@ -822,7 +851,11 @@ int triot_batch_plan_create(const triot_batch_desc* descs, int n, int dtype, int
   p->npairs = n;
   p->ntiles = ntiles;
   p->descs.assign(descs, descs + n);
-  const int cps = (tune && tune->ctas_per_sm > 0) ? tune->ctas_per_sm : 4;
+  const int cps = (tune && tune->ctas_per_sm > 0) ? tune->ctas_per_sm
+                  : tuned.ctas_per_sm > 0           ? tuned.ctas_per_sm
+                                                    : 4;
+  p->tile_elems = (int)target;
+  p->ctas_per_sm = cps;
   p->nxtiles = nxtiles;
   p->nfill = nfill;
   p->grid = (int)std::max(1ll, std::min<long long>((ntiles + kBatchWarps - 1) / kBatchWarps, (long long)dev.sms * cps));
@@ -898,8 +931,75 @@ int triot_batch_plan_info(const triot_plan* p, size_t* device_bytes, int64_t* ti
   return ok();
 }
 
+int triot_batch_plan_geometry(const triot_plan* p, triot_tune* out) {
+  if (!p || !out) return fail(TRIOT_ERR_NULL, "plan or out is NULL");
+  out->threads = kBatchThreads;
+  out->tile_elems = p->tile_elems;
+  out->ctas_per_sm = p->ctas_per_sm;
+  out->unroll = 0;
+  return ok();
+}
+
 int triot_batch_plan_destroy(triot_plan* p) {
   free_plan(p);
+  return ok();
+}
+
+int triot_batch_autotune(const triot_batch_desc* descs, int n, int dtype, int mode, void* stream,
+                         triot_tune* best) {
+  if (!descs || n <= 0) return fail(TRIOT_ERR_ARG, "need at least one descriptor");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  float best_ms = 1e30f;
+  triot_tune best_t{0, 0, 0, 0};
+  int rc = TRIOT_OK;
+  for (int tile : {256, 512, 1024, 2048, 4096}) {
+    for (int cps : {2, 4, 8}) {
+      triot_tune t{0, tile, cps, 0};
+      triot_plan* p = nullptr;
+      if ((rc = triot_batch_plan_create(descs, n, dtype, mode, &t, &p))) break;
+      // the first run captures the graph; it and one more are warm-up
+      for (int w = 0; w < 2 && rc == TRIOT_OK; ++w) rc = triot_batch_run(p, stream);
+      std::vector<float> ms;
+      for (int r = 0; r < 3 && rc == TRIOT_OK; ++r) {
+        cudaEventRecord(a, s);
+        rc = triot_batch_run(p, stream);
+        cudaEventRecord(b, s);
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) { rc = cuda_fail(e, "batch autotune"); break; }
+        float v = 0.f;
+        cudaEventElapsedTime(&v, a, b);
+        ms.push_back(v);
+      }
+      triot_batch_plan_destroy(p);
+      if (rc) break;
+      std::sort(ms.begin(), ms.end());
+      if (ms[ms.size() / 2] < best_ms) {
+        best_ms = ms[ms.size() / 2];
+        best_t = t;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  long long ny_total = 0;
+  for (int i = 0; i < n; ++i) {
+    long long ny = 1;
+    for (int ax = 0; ax < descs[i].rank; ++ax) ny *= descs[i].yshape[ax];
+    ny_total += ny;
+  }
+  TuneCfg tc;
+  tc.tile_elems = best_t.tile_elems;
+  tc.ctas_per_sm = best_t.ctas_per_sm;
+  tune_store_key(batch_key(dtype, mode, n, ny_total), tc);
+  if (best) *best = best_t;
   return ok();
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "sync.cuh"
 
 namespace triot {
 
@@ -46,14 +47,7 @@ __device__ __forceinline__ void fm_cp16(void* smem, const void* gmem, int src_by
 // bounded wait for the phase of parity `par` of the mbarrier at shared address `bar`; on
 // time-out the sticky flag is set (lane 0) and the caller goes on, so the kernel ends
 __device__ __forceinline__ void fm_wait(unsigned bar, unsigned par, int lane, int* flag) {
-  unsigned done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
-    asm volatile(
-        "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
-        : "=r"(done)
-        : "r"(bar), "r"(par)
-        : "memory");
-  if (!done && lane == 0) atomicExch(flag, 1);
+  if (!mbar_wait_bounded(bar, par, kWaitLimit) && lane == 0) atomicExch(flag, 1);
 }
 
 // one window sum of every lane into the warp's total: f32 xor tree (a fixed order), then a

@@ -37,8 +37,14 @@ int moment_call(int rank, const int64_t* shape, const void* p, int dtype, double
 // tuning cache (tune.cpp)
 TuneCfg tune_lookup(int op, int dtype, const Canon& c);
 void tune_store(int op, int dtype, const Canon& c, const TuneCfg& t);
+// batches (TRIOT_OP_BATCH): keyed by dtype, mode and size class
+std::string batch_key(int dtype, int mode, long long npairs, long long ny_total);
+TuneCfg tune_lookup_key(const std::string& k);
+void tune_store_key(const std::string& k, const TuneCfg& t);
 
 // device-side guard flag (batch.cu)
 void st_read_device_flag(int* flag);
+// the bounded-wait self-test's flag (selftest.cu)
+void selftest_read_device_flag(int* flag);
 
 }  // namespace triot

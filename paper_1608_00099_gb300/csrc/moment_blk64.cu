@@ -32,6 +32,7 @@
 
 #include "kernels.h"
 #include "moment.cuh"
+#include "sync.cuh"
 
 namespace triot {
 namespace {
@@ -180,14 +181,7 @@ __global__ void __launch_bounds__(kB64Warps * 32, 6) moment_b64_kernel(
   auto wait_stage = [&](int q) {
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp][q]);
     const unsigned par = (phase >> q) & 1u;
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-      asm volatile(
-          "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
-          : "=r"(done)
-          : "r"(bar), "r"(par)
-          : "memory");
-    if (!done && lane == 0) atomicExch(&g_b64_flag, 1);
+    if (!mbar_wait_bounded(bar, par, kWaitLimit) && lane == 0) atomicExch(&g_b64_flag, 1);
     phase ^= 1u << q;
   };
 

@@ -76,6 +76,29 @@ void tune_store(int op, int dtype, const Canon& c, const TuneCfg& t) {
   g_cache[k] = t;
 }
 
+// A batch is keyed by its dtype, mode and size class: floor(log2) of its pair count and of
+// its total number of y elements.
+std::string batch_key(int dtype, int mode, long long npairs, long long ny_total) {
+  DeviceInfo dev;
+  const char* name = "gpu";
+  if (device_info(dev) == TRIOT_OK) name = dev.name;
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s|op%d|dt%d|mode%d|n%d|y%d", name, TRIOT_OP_BATCH, dtype, mode,
+           inner_class(npairs), inner_class(ny_total));
+  return buf;
+}
+
+TuneCfg tune_lookup_key(const std::string& k) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_cache.find(k);
+  return it == g_cache.end() ? TuneCfg() : it->second;
+}
+
+void tune_store_key(const std::string& k, const TuneCfg& t) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cache[k] = t;
+}
+
 }  // namespace triot
 
 using namespace triot;

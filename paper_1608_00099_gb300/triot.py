@@ -79,6 +79,8 @@ def lib() -> C.CDLL:
             "triot_batch_run_plain": (i, [vp, vp]),
             "triot_batch_plan_info": (i, [vp, C.POINTER(sz), _I64P]),
             "triot_batch_plan_destroy": (i, [vp]),
+            "triot_batch_plan_geometry": (i, [vp, C.POINTER(Tune)]),
+            "triot_batch_autotune": (i, [C.POINTER(BatchDesc), i, i, i, vp, C.POINTER(Tune)]),
             "triot_autotune": (i, [i, i, _I64P, vp, _I64P, vp, i, vp, sz, vp, C.POINTER(Tune)]),
             "triot_tune_get": (i, [i, i, _I64P, _I64P, i, C.POINTER(Tune)]),
             "triot_tune_set": (i, [i, i, _I64P, _I64P, i, C.POINTER(Tune)]),
@@ -90,6 +92,7 @@ def lib() -> C.CDLL:
             "triot_fastdiv_check": (i, [C.c_uint32, C.POINTER(C.c_uint32), sz, C.POINTER(C.c_uint32),
                                         C.POINTER(C.c_uint32)]),
             "triot_device_status": (i, []),
+            "triot_selftest_wait_timeout": (i, [i, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -299,6 +302,10 @@ def triot_device_status() -> int:
     return int(lib().triot_device_status())
 
 
+def triot_selftest_wait_timeout(limit: int = 16, stream=None) -> None:
+    _check(lib().triot_selftest_wait_timeout(limit, _stream(stream)))
+
+
 # ------------------------------------------------------------------ tuning
 
 def _tune_dict(t: Tune) -> dict:
@@ -349,23 +356,36 @@ def triot_tune_clear() -> None:
 
 # ------------------------------------------------------------------ batched pipeline
 
+def _batch_descs(xs, ys, outs):
+    if not (len(xs) == len(ys) == len(outs)) or not xs:
+        raise TriotError(8, "need matching, non-empty lists of x, y and out")
+    dt = _dtype(xs[0])
+    descs = (BatchDesc * len(xs))()
+    for k, (x, y, o) in enumerate(zip(xs, ys, outs)):
+        if x.dim() != y.dim() or _dtype(x) != dt or _dtype(y) != dt:
+            raise TriotError(8, f"pair {k}: ranks or dtypes differ")
+        d = descs[k]
+        d.rank = x.dim()
+        for a in range(x.dim()):
+            d.xshape[a] = x.shape[a]
+            d.yshape[a] = y.shape[a]
+        d.x, d.y, d.moment_out = _dev(x), _dev(y), _dev(o)
+    return descs, dt
+
+
+def triot_batch_autotune(xs, ys, outs, mode: int = 0, stream=None) -> dict:
+    """Time the batch's candidate geometries and cache the fastest (triot_batch_autotune)."""
+    descs, dt = _batch_descs(xs, ys, outs)
+    best = Tune()
+    _check(lib().triot_batch_autotune(descs, len(xs), dt, mode, _stream(stream), C.byref(best)))
+    return _tune_dict(best)
+
+
 class BatchPlan:
     """Owns a triot_plan: embed -> product -> moment for many (x, y, out) triples."""
 
     def __init__(self, xs, ys, outs, mode: int = BATCH_FUSED, tile_elems: int = 0, ctas_per_sm: int = 0):
-        if not (len(xs) == len(ys) == len(outs)) or not xs:
-            raise TriotError(8, "need matching, non-empty lists of x, y and out")
-        dt = _dtype(xs[0])
-        descs = (BatchDesc * len(xs))()
-        for k, (x, y, o) in enumerate(zip(xs, ys, outs)):
-            if x.dim() != y.dim() or _dtype(x) != dt or _dtype(y) != dt:
-                raise TriotError(8, f"pair {k}: ranks or dtypes differ")
-            d = descs[k]
-            d.rank = x.dim()
-            for a in range(x.dim()):
-                d.xshape[a] = x.shape[a]
-                d.yshape[a] = y.shape[a]
-            d.x, d.y, d.moment_out = _dev(x), _dev(y), _dev(o)
+        descs, dt = _batch_descs(xs, ys, outs)
         self._keep = (xs, ys, outs)
         self._h = C.c_void_p(0)
         tune = Tune(0, tile_elems, ctas_per_sm, 0)
@@ -382,6 +402,11 @@ class BatchPlan:
         t = C.c_int64(0)
         _check(lib().triot_batch_plan_info(self._h, C.byref(b), C.byref(t)))
         return {"device_bytes": int(b.value), "tiles": int(t.value)}
+
+    def geometry(self) -> dict:
+        t = Tune()
+        _check(lib().triot_batch_plan_geometry(self._h, C.byref(t)))
+        return _tune_dict(t)
 
     def close(self) -> None:
         if self._h:

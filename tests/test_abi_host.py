@@ -170,3 +170,77 @@ def test_tune_cache_roundtrip_without_gpu(tr, tmp_path):
     bad = tr.Tune(33, 0, 0, 0)
     assert L.triot_tune_set(0, 2, tr._shape((2, 3)), tr._shape((4, 5)), 0, C.byref(bad)) == 8
     assert L.triot_tune_load(str(tmp_path / "missing.json").encode()) == 8
+
+
+def _desc(tr, xs, ys, x=0x1000, y=0x10000000, out=0x20000000):
+    d = tr.BatchDesc()
+    d.rank = len(xs)
+    for a, (e, f) in enumerate(zip(xs, ys)):
+        d.xshape[a] = e
+        d.yshape[a] = f
+    d.x, d.y, d.moment_out = x, y, out
+    return d
+
+
+@pytest.mark.parametrize("case,code", [
+    ("negative extent", 2), ("zero extent", 2), ("x larger than y", 2), ("extent 2^31", 2),
+    ("rank 0", 1), ("rank 25", 1), ("rank -3", 1), ("null x", 3), ("null y", 3), ("null out", 3),
+    ("x overlaps y", 6), ("too many elements", 2)])
+def test_batch_plan_rejects_corrupted_descriptor(tr, case, code):
+    """A corrupted descriptor anywhere in the list fails plan creation with its status code
+    before any device memory is allocated (no GPU is present here)."""
+    import ctypes as C
+    L = tr.lib()
+    good = [_desc(tr, (2, 3), (4, 5), x=0x1000 + k * 0x100000, y=0x40000000 + k * 0x100000) for k in range(5)]
+    bad = _desc(tr, (2, 3), (4, 5), x=0x7000000, y=0x8000000)
+    if case == "negative extent":
+        bad.xshape[1] = -3
+    elif case == "zero extent":
+        bad.yshape[0] = 0
+    elif case == "x larger than y":
+        bad.xshape[0] = 9
+    elif case == "extent 2^31":
+        bad.xshape[1] = 1
+        bad.yshape[1] = 1 << 31
+    elif case == "rank 0":
+        bad.rank = 0
+    elif case == "rank 25":
+        bad.rank = 25
+    elif case == "rank -3":
+        bad.rank = -3
+    elif case == "null x":
+        bad.x = None
+    elif case == "null y":
+        bad.y = None
+    elif case == "null out":
+        bad.moment_out = None
+    elif case == "x overlaps y":
+        bad.y = bad.x + 8
+    elif case == "too many elements":
+        bad.rank = 6
+        for a in range(6):
+            bad.xshape[a] = 2
+            bad.yshape[a] = 1 << 20
+    descs = (tr.BatchDesc * 6)(*(good[:3] + [bad] + good[3:]))
+    plan = C.c_void_p(0)
+    assert L.triot_batch_plan_create(descs, 6, 1, 0, None, C.byref(plan)) == code
+    assert not plan.value
+    assert "descriptor 3" in L.triot_last_error().decode()
+
+
+def test_batch_plan_rejects_bad_arguments(tr):
+    import ctypes as C
+    L = tr.lib()
+    descs = (tr.BatchDesc * 1)(_desc(tr, (2, 3), (4, 5)))
+    plan = C.c_void_p(0)
+    assert L.triot_batch_plan_create(descs, 0, 1, 0, None, C.byref(plan)) == 8        # no pairs
+    assert L.triot_batch_plan_create(None, 1, 1, 0, None, C.byref(plan)) == 8
+    assert L.triot_batch_plan_create(descs, 1, 7, 0, None, C.byref(plan)) == 4        # dtype
+    assert L.triot_batch_plan_create(descs, 1, 1, 5, None, C.byref(plan)) == 8        # mode
+    assert L.triot_batch_plan_create(descs, 1, 1, 0, None, None) == 3
+    t = tr.Tune(0, -1, 0, 0)
+    assert L.triot_batch_plan_create(descs, 1, 1, 0, C.byref(t), C.byref(plan)) == 8  # tile < 0
+    t = tr.Tune(0, 0, 33, 0)
+    assert L.triot_batch_plan_create(descs, 1, 1, 0, C.byref(t), C.byref(plan)) == 8  # ctas/SM
+    assert L.triot_batch_autotune(None, 1, 1, 0, None, None) == 8
+    assert not plan.value

@@ -137,6 +137,59 @@ def test_embed_guard_band_untouched(tr):
     assert np.all(h[:32] == -1.0) and np.all(h[32 + n:] == -1.0)
 
 
+def _guarded(shape, dtype, fill, band=40):
+    """A tensor of `shape` inside a buffer with `band` sentinel elements on each side."""
+    n = int(np.prod(shape))
+    buf = torch.full((n + 2 * band,), fill, dtype=TORCH[dtype], device="cuda")
+    return buf, buf[band:band + n].view(shape)
+
+
+def _band_intact(buf, n, dtype, fill, band=40):
+    h = to_host(buf, dtype)
+    f = to_host(torch.full((1,), fill, dtype=TORCH[dtype]).cuda(), dtype)[0]
+    return np.all(h[:band] == f) and np.all(h[band + n:] == f)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("shapes", [((9,) * 4, (12, 8, 12, 8)), ((7, 13, 6), (9, 16, 8)), ((3, 3000), (4, 9001))])
+def test_product_and_crop_guard_bands_untouched(tr, dtype, shapes):
+    xs, ys = shapes
+    xh = host_values(int(np.prod(xs)), dtype, 41, law="uniform")
+    yh = host_values(int(np.prod(ys)), dtype, 42)
+    x = to_dev(xh, dtype, xs)
+    ybuf, y = _guarded(ys, dtype, -3)
+    y.copy_(to_dev(yh, dtype, ys))
+    tr.triot_product(x, y)
+    assert to_host(y, dtype).tobytes() == orc.product(xh, xs, yh, ys, dtype).tobytes()
+    assert _band_intact(ybuf, int(np.prod(ys)), dtype, -3)
+    cs = tuple(min(a, b) for a, b in zip(xs, ys))
+    cbuf, c = _guarded(cs, dtype, -5)
+    tr.triot_crop(c, y)
+    ref = orc.crop(orc.product(xh, xs, yh, ys, dtype), cs, ys, dtype)
+    assert to_host(c, dtype).tobytes() == ref.tobytes()
+    assert _band_intact(cbuf, int(np.prod(cs)), dtype, -5)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
+def test_views_guard_bands_untouched(tr, dtype):
+    xs, ys, st = (5, 6, 7), (9, 11, 13), (2, 3, 5)
+    xh = host_values(int(np.prod(xs)), dtype, 43, law="uniform")
+    ny = int(np.prod(ys))
+    x = to_dev(xh, dtype, xs)
+    ybuf, y = _guarded(ys, dtype, -7)
+    tr.triot_embed_at(x, y, st)
+    assert to_host(y, dtype).tobytes() == orc.embed_at(xh, xs, ys, st, dtype).tobytes()
+    assert _band_intact(ybuf, ny, dtype, -7)
+    xbuf, x2 = _guarded(xs, dtype, -9)
+    tr.triot_crop_at(x2, y, st)
+    assert to_host(x2, dtype).tobytes() == xh.tobytes()
+    assert _band_intact(xbuf, int(np.prod(xs)), dtype, -9)
+    yh = to_host(y, dtype).copy()
+    tr.triot_product_at(x, y, st)
+    assert to_host(y, dtype).tobytes() == orc.product_at(xh, xs, yh, ys, st, dtype).tobytes()
+    assert _band_intact(ybuf, ny, dtype, -7)
+
+
 # ---------------------------------------------------------------- product
 
 PROD_SHAPES = [
@@ -248,12 +301,40 @@ def test_moment_f64_wide_dynamic_range_and_subnormals(tr):
     check_moment(got, ref, moment_scale(v, shape, "f64"), 1e-12)
 
 
-def test_moment_f64_nonfinite_propagates(tr):
-    shape = (20, 33)
-    v = synth.uniform01(5, 660)
-    v[100] = np.inf
+def _same_moment_with_specials(got, ref, scale, tol):
+    """Non-finite components must match the oracle's class exactly (the same infinity, or
+    NaN on both sides); finite ones within the tolerance."""
+    for g, r, sc in zip(got, ref, scale):
+        if np.isnan(r):
+            assert np.isnan(g), (got, ref)
+        elif np.isinf(r):
+            assert g == r, (got, ref)
+        else:
+            assert np.isfinite(g) and abs(g - r) <= tol * sc + 1e-300, (got, ref)
+
+
+@pytest.mark.parametrize("case", ["inf", "inf_zero_digit", "both_infinities", "nan", "neg_inf_signed"])
+@pytest.mark.parametrize("shape", [(20, 33), (9, 9, 9, 9), (40, 7, 3)])
+def test_moment_f64_nonfinite_against_oracle(tr, case, shape):
+    n = int(np.prod(shape))
+    v = synth.uniform01(5, n)
+    if case == "inf":
+        v[n // 2 + 1] = np.inf
+    elif case == "inf_zero_digit":
+        v[0] = np.inf                      # tuple (0, ..., 0): inf * 0 is NaN in every moment
+    elif case == "both_infinities":
+        v[n // 3] = np.inf
+        v[2 * n // 3] = -np.inf
+    elif case == "nan":
+        v[n - 1] = np.nan
+    else:
+        v = v - 0.5
+        v[n // 5] = -np.inf
+    ref = orc.moment(v, shape, "f64")
     got = tr.triot_moment(torch.from_numpy(v.reshape(shape)).cuda()).cpu().numpy()
-    assert not np.isfinite(got[-1]) and np.all(~np.isfinite(got[:2]) | (got[:2] != got[:2]))
+    scale = moment_scale(np.where(np.isfinite(v), v, 0.0), shape, "f64")
+    assert not np.all(np.isfinite(ref))
+    _same_moment_with_specials(got, ref, scale, 1e-12)
 
 
 def test_moment_unaligned_input(tr):

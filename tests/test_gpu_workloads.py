@@ -1,5 +1,8 @@
 """Parity at the full workload sizes, in the launch configuration bench.py times.
 
+The f64 d=8 step runs twice: under the default geometry and under the committed tuning
+file that bench.py loads before it times the step (paper_1608_00099_gb300/tune_gb300.json).
+
 Small and medium cases are compared in full; the 44 GB embed target of the f32 d=24
 workload is compared on windows the oracle computes one element at a time, and through
 properties that hold at any size (pad count, crop round trip).
@@ -40,6 +43,19 @@ def test_embed_f64_d6_full(tr):
     assert torch.equal(x2, x)
 
 
+TUNE_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                         "paper_1608_00099_gb300", "tune_gb300.json")
+
+
+@pytest.fixture(params=["default", "tuned"])
+def geometry(request, tr):
+    tr.triot_tune_clear()
+    if request.param == "tuned":
+        tr.triot_tune_load(TUNE_FILE)
+    yield request.param
+    tr.triot_tune_clear()
+
+
 @pytest.fixture(scope="module")
 def f64_d8():
     cfg = synth.config_f64_d8()
@@ -47,7 +63,7 @@ def f64_d8():
     return cfg, xh
 
 
-def test_f64_d8_embed_full(tr, f64_d8):
+def test_f64_d8_embed_full(tr, f64_d8, geometry):
     cfg, xh = f64_d8
     x = torch.from_numpy(xh.reshape(cfg.xshape)).cuda()
     y = torch.empty(cfg.embed_shape, dtype=torch.float64, device="cuda")
@@ -59,7 +75,7 @@ def test_f64_d8_embed_full(tr, f64_d8):
     assert torch.equal(x2, x)
 
 
-def test_f64_d8_product_full(tr, f64_d8):
+def test_f64_d8_product_full(tr, f64_d8, geometry):
     cfg, xh = f64_d8
     yh = cfg.yprod_values()
     x = torch.from_numpy(xh.reshape(cfg.xshape)).cuda()
@@ -69,7 +85,7 @@ def test_f64_d8_product_full(tr, f64_d8):
     assert np.array_equal(y.cpu().numpy().reshape(-1).view(np.uint64), ref.view(np.uint64))
 
 
-def test_f64_d8_moment_full(tr, f64_d8):
+def test_f64_d8_moment_full(tr, f64_d8, geometry):
     cfg, xh = f64_d8
     ph = synth.normalise(xh)
     p = torch.from_numpy(ph.reshape(cfg.xshape)).cuda()
