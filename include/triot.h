@@ -327,7 +327,9 @@ int triot_batch_autotune(const triot_batch_desc* descs, int n, int dtype, int mo
  * triot_autotune -- time candidate launch geometries for one (op, rank, shapes, dtype)
  *   on the caller's buffers (which it overwrites exactly as the op would) with CUDA
  *   events on `stream`, keep the fastest in the in-process cache (keyed by GPU, op,
- *   dtype, effective rank and inner-extent class) and return it in *best.  For
+ *   dtype, effective rank and inner-extent class) and return it in *best.  x and y are
+ *   the op's own arguments in the op's order (TRIOT_OP_CROP writes x and reads y, despite
+ *   the const on x here; embed and product write y).  For
  *   TRIOT_OP_MOMENT pass p as `x`, NULL as `y`, and a workspace large enough for every
  *   candidate (triot_moment_workspace_size with the largest geometry: use
  *   TRIOT_MOMENT_MAX_WORKSPACE_PER_RANK * (rank + 1) bytes).  Synchronises `stream`.
@@ -374,6 +376,23 @@ int triot_canonicalize(int op, int rank, const int64_t* xshape, const int64_t* y
  *   (1 <= d < 2^31) and writes quotients q[k] and remainders r[k].  For tests.
  */
 int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q, uint32_t* r);
+
+/*
+ * triot_moment_plan -- which moment kernel triot_moment would launch for this shape and
+ *   dtype under the tuning in force (no GPU work; needs the device's properties):
+ *   *kernel = TRIOT_MK_ROWS (lane segments along the inner axis), TRIOT_MK_BLOCKS64 (f64
+ *   block columns), TRIOT_MK_BLOCKS32 (float block columns), TRIOT_MK_WARPBLOCKS (float
+ *   warp blocks) or TRIOT_MK_MARGINALS (f64 rows x columns split), *grid = its CTAs (the
+ *   partial vectors the combine adds), and for TRIOT_MK_MARGINALS *rows / *cols the matrix
+ *   view (else 0).  Any output pointer may be NULL.
+ */
+#define TRIOT_MK_ROWS 0
+#define TRIOT_MK_BLOCKS64 1
+#define TRIOT_MK_BLOCKS32 2
+#define TRIOT_MK_WARPBLOCKS 3
+#define TRIOT_MK_MARGINALS 4
+int triot_moment_plan(int rank, const int64_t* shape, int dtype, int* kernel, int* grid,
+                      int64_t* rows, int64_t* cols);
 
 /* Sticky device-side status (TRIOT_OK or TRIOT_ERR_DEVICE) of the current device; reading
  * it synchronises the device and clears it.  It is set when a kernel's bounded wait for a

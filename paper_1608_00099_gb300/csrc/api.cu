@@ -145,6 +145,15 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
   if (st) return fail(st, err);
   DeviceInfo dev;
   if ((st = device_info(dev))) return st;
+  TuneCfg t = force ? *force : tune_lookup(TRIOT_OP_MOMENT, dtype, c);
+  if (dtype == DT_F64) {
+    // the marginal split when the axes give good rows and columns
+    const void* fmx = moment_mx64_kernel_ptr();
+    int occ = 1;
+    if ((st = moment_occupancy(fmx, kMxWarps * 32, 0, 0, occ))) return st;
+    const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
+    if (plan_moment_mx(c, rank, (long long)dev.sms * cps * kMxWarps, L)) return TRIOT_OK;
+  }
   const int m = moment_block_axes(c, dtype);
   int B = 1;
   for (int a = c.D - m; a < c.D; ++a) B *= (int)c.ext[a];
@@ -163,7 +172,7 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
                          : wb ? (size_t)wb_dyn_smem(kMaxRank - 1, wb_vec(Bk, es)) : 0;
   const int threads = (b64 ? kB64Warps : b32 ? kB32Warps : wb ? kWBWarps : kMomentWarps) * 32;
   if ((st = moment_occupancy(fn, threads, dyn, dyn_max, occ))) return st;
-  TuneCfg t = force ? *force : tune_lookup(TRIOT_OP_MOMENT, dtype, c);
+  L.kind = MOMENT_KIND_ROWS_BLOCKS;
   plan_moment(c, rank, dtype_size(dtype), m, p, t, dev, occ, L);
   L.smem = dyn;
   if (L.grid > kMaxMomentParts) return fail(TRIOT_ERR_ARG, "moment grid exceeds the partial limit");
@@ -178,7 +187,12 @@ size_t moment_ws_bytes(const MomentLaunch& L) {
 int launch_moment(const MomentLaunch& L, int dtype, const void* p, double* out, void* ws,
                   cudaStream_t stream) {
   cudaError_t e;
-  if (!L.empty) {
+  if (L.kind == MOMENT_KIND_MX) {
+    double* part = static_cast<double*>(ws);
+    void* args[] = {(void*)&L.mx, (void*)&p, (void*)&part};
+    e = cudaLaunchKernel(moment_mx64_kernel_ptr(), dim3(L.grid), dim3(L.warps * 32), args, 0, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moment kernel launch");
+  } else if (!L.empty) {
     const void* fn = moment_kernel_ptr(dtype, L.g.D, L.g.m, L.g.B);
     if (!fn) return fail(TRIOT_ERR_RANK, "no moment kernel for this effective rank");
     double* part = static_cast<double*>(ws);
@@ -244,6 +258,23 @@ int triot_moment_workspace_size(int rank, const int64_t* shape, int dtype, size_
   int st = plan_moment_call(rank, shape, dtype, nullptr, nullptr, L);
   if (st) return st;
   *bytes = moment_ws_bytes(L);
+  return ok();
+}
+
+int triot_moment_plan(int rank, const int64_t* shape, int dtype, int* kernel, int* grid, int64_t* rows,
+                      int64_t* cols) {
+  MomentLaunch L;
+  int st = plan_moment_call(rank, shape, dtype, nullptr, nullptr, L);
+  if (st) return st;
+  int k = TRIOT_MK_ROWS;
+  if (L.kind == MOMENT_KIND_MX) k = TRIOT_MK_MARGINALS;
+  else if (L.g.m > 0 && dtype == DT_F64) k = TRIOT_MK_BLOCKS64;
+  else if (L.g.m > 0 && L.g.B >= 32) k = TRIOT_MK_WARPBLOCKS;
+  else if (L.g.m > 0) k = TRIOT_MK_BLOCKS32;
+  if (kernel) *kernel = k;
+  if (grid) *grid = L.empty ? 0 : L.grid;
+  if (rows) *rows = L.kind == MOMENT_KIND_MX ? L.mx.R : 0;
+  if (cols) *cols = L.kind == MOMENT_KIND_MX ? L.mx.C : 0;
   return ok();
 }
 

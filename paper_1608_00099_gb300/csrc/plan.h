@@ -5,6 +5,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "mx.cuh"
 
 namespace triot {
 
@@ -44,11 +45,17 @@ void plan_rows(int op, const Canon& c, bool x_empty, int es, const void* A, cons
 struct MomentLaunch {
   MomentGeom g;
   CombineGeom cg;
+  int kind = 0;        // MOMENT_KIND_* below
+  MxGeom mx;           // MOMENT_KIND_MX: the marginal split
   int grid = 0;        // CTAs of the moment kernel (= number of partial vectors)
   int warps = 4;       // warps per CTA
   size_t smem = 0;     // dynamic shared memory per CTA (block kernels: stages, outer-axis state)
   bool empty = false;  // nothing to sum: only the combine runs (it writes zeros)
 };
+enum { MOMENT_KIND_ROWS_BLOCKS = 0, MOMENT_KIND_MX = 1 };
+// The marginal split of a f64 moment (moment_mx.cu): false when no split of the canonical
+// axes gives rows and columns the kernel can use well.  `target_warps` = warps of a full GPU.
+bool plan_moment_mx(const Canon& c, int rank, long long target_warps, MomentLaunch& L);
 // `occ` = resident CTAs per SM of the chosen kernel (from the occupancy calculator).
 void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
                  const DeviceInfo& dev, int occ, MomentLaunch& L);

@@ -114,6 +114,69 @@ int moment_block_axes(const Canon& c, int dtype) {
   return axes(16, b);
 }
 
+bool plan_moment_mx(const Canon& c, int rank, long long target_warps, MomentLaunch& L) {
+  if (c.empty || c.D < 2) return false;
+  constexpr long long W = 32 * kMxJ;  // columns of a warp tile
+  // split after axis s-1: the best use of the tiles' columns, then columns near 2^12
+  int best_s = 0;
+  double best_score = -1.0;
+  for (int s = 1; s < c.D; ++s) {
+    long long C = 1, R = 1;
+    for (int a = s; a < c.D; ++a) C *= c.ext[a];
+    for (int a = 0; a < s; ++a) R *= c.ext[a];
+    if (C >= (1ll << 31) || R >= (1ll << 31) || C < W / 2) continue;
+    const long long tiles = (C + W - 1) / W;
+    const double eff = double(C) / double(tiles * W);
+    if (eff < 0.8) continue;
+    double lc = 0.0;
+    for (long long v = C; v > 1; v >>= 1) lc += 1.0;
+    const double score = eff - 0.01 * (lc > 12.0 ? lc - 12.0 : 12.0 - lc);
+    if (score > best_score) {
+      best_score = score;
+      best_s = s;
+    }
+  }
+  if (best_s == 0) return false;
+  MxGeom& g = L.mx;
+  g = MxGeom();
+  g.D = c.D;
+  g.s = best_s;
+  g.C = 1;
+  g.R = 1;
+  for (int a = best_s; a < c.D; ++a) g.C *= c.ext[a];
+  for (int a = 0; a < best_s; ++a) g.R *= c.ext[a];
+  for (int i = 0; i < c.D; ++i) {
+    g.ext[i] = c.ext[i];
+    g.div[i] = make_fastdiv((uint32_t)c.ext[i]);
+  }
+  g.r32 = g.R < (1ll << 32);
+  g.tiles = (g.C + W - 1) / W;
+  // one warp per (tile, row range): enough ranges to fill the GPU, whole warps per CTA
+  long long parts = std::max(1ll, std::min(g.R, target_warps / g.tiles));
+  g.parts = parts;
+  const long long rows_per_warp = (g.R + parts - 1) / parts;
+  g.win = (int)std::min<long long>(kMxWindow, std::max(1ll, rows_per_warp));
+  const long long warps = g.tiles * parts;
+  const long long grid = (warps + kMxWarps - 1) / kMxWarps;
+  if (grid > kMxMaxGrid) return false;
+  L.kind = MOMENT_KIND_MX;
+  L.grid = (int)grid;
+  L.warps = kMxWarps;
+  L.smem = 0;
+  L.empty = false;
+  // the row/block geometry is unused, but the effective rank must be right for the
+  // workspace size and the combine
+  L.g = MomentGeom();
+  L.g.D = c.D;
+  CombineGeom& cg = L.cg;
+  cg = CombineGeom();
+  cg.D = c.D;
+  cg.rank = rank;
+  cg.nparts = L.grid;
+  for (int i = 0; i < c.D; ++i) cg.orig[i] = c.orig[i];
+  return true;
+}
+
 void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
                  const DeviceInfo& dev, int occ, MomentLaunch& L) {
   MomentGeom& g = L.g;

@@ -238,7 +238,7 @@ int triot_autotune(int op, int rank, const int64_t* xshape, const void* x, const
   auto run = [&](const TuneCfg& t) -> int {
     if (op == TRIOT_OP_MOMENT) return moment_call(rank, xshape, x, dtype, out, workspace, workspace_bytes, s, &t);
     const int rop = op == TRIOT_OP_EMBED ? ROW_EMBED : op == TRIOT_OP_CROP ? ROW_CROP : ROW_PRODUCT;
-    if (rop == ROW_CROP) return launch_rows(rop, rank, xshape, y, yshape, x, dtype, 0, s, &t);
+    // same argument order as triot_embed / triot_crop / triot_product (crop writes x)
     return launch_rows(rop, rank, xshape, x, yshape, y, dtype, 0, s, &t);
   };
   cudaEvent_t a, b;

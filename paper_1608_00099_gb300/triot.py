@@ -67,6 +67,7 @@ def lib() -> C.CDLL:
             "triot_moment_workspace_size": (i, [i, _I64P, i, C.POINTER(sz)]),
             "triot_moment": (i, [i, _I64P, vp, i, vp, vp, sz, vp]),
             "triot_moment_noalloc": (i, [i, _I64P, vp, i, vp, vp]),
+            "triot_moment_plan": (i, [i, _I64P, i, C.POINTER(i), C.POINTER(i), _I64P, _I64P]),
             "triot_apply": (i, [i, i, _I64P, vp, _I64P, vp, _I64P, vp, i, vp]),
             "triot_convolve": (i, [i, _I64P, vp, _I64P, vp, vp, i, vp]),
             "triot_embed_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, u, vp]),
@@ -190,6 +191,18 @@ def triot_moment(p: torch.Tensor, out: torch.Tensor | None = None, workspace: to
     _check(lib().triot_moment(rank, _shape(p.shape), _dev(p), _dtype(p), _dev(out), _dev(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
     return out
+
+
+MOMENT_KERNELS = {0: "rows", 1: "blocks64", 2: "blocks32", 3: "warpblocks", 4: "marginals"}
+
+
+def triot_moment_plan(shape, dtype: torch.dtype) -> dict:
+    """The moment kernel triot_moment would launch for this shape and dtype."""
+    k, g = C.c_int(0), C.c_int(0)
+    r, c = C.c_int64(0), C.c_int64(0)
+    _check(lib().triot_moment_plan(len(shape), _shape(shape), DTYPE_CODE[dtype], C.byref(k), C.byref(g),
+                                   C.byref(r), C.byref(c)))
+    return {"kernel": MOMENT_KERNELS[k.value], "grid": g.value, "rows": r.value, "cols": c.value}
 
 
 def triot_convolve(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
