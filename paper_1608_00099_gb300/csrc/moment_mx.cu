@@ -5,9 +5,11 @@
 // way: for a row axis i,  m_i = sum over rows r of  t_i(r) * (mass of row r),  and for a
 // column axis a,  m_a = sum over columns c of  t_a(c) * (mass of column c).  Each warp owns
 // one tile of 32*J columns (lane l holds columns l, l + 32, ..., l + 32(J-1) of the tile)
-// and a contiguous range of rows; rows are streamed in order with coalesced loads straight
-// from HBM (no staging), so every element costs one load, its conversion to fixed point and
-// two integer adds: one into its column's sum, one into the lane's part of the row's mass.
+// and a contiguous range of rows.  Each row's segment of the tile (up to 2 KB, contiguous)
+// is staged into shared memory by one bulk copy issued by lane 0, kMxStages rows ahead, so
+// the loads in flight cost no registers; every element then costs one shared-memory read,
+// its conversion to fixed point and two integer adds: one into its column's sum, one into
+// the lane's part of the row's mass.
 // The row's digits are the same for the whole warp and advance like Algorithm 3 (one
 // increment per row, carries at wraps), so the tuple arithmetic is per row, not per
 // element:
@@ -29,9 +31,13 @@
 #include "mx.cuh"
 #include "fixed.cuh"
 #include "kernels.h"
+#include "sync.cuh"
 
 namespace triot {
 namespace {
+
+// set when a bounded wait for a staged row gives up (read by triot_device_status)
+__device__ int g_mx_flag = 0;
 
 // c = m >> sh for sh in [0, 2^32): the PTX shift clamps amounts above 64 (result 0)
 __device__ __forceinline__ unsigned long long shr_clamp(unsigned long long m, uint32_t sh) {
@@ -79,8 +85,18 @@ __device__ __noinline__ void mx_special(const MxGeom& g, double v, const uint32_
 template <int J>
 __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
     const __grid_constant__ MxGeom g, const double* __restrict__ p, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double wsum[kMxWarps][kMaxRank + 1];
+  __shared__ __align__(8) unsigned long long s_bar[kMxWarps][kMxStages];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    for (int q = 0; q < kMxStages; ++q) {
+      const unsigned a = (unsigned)__cvta_generic_to_shared(&s_bar[warp][q]);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
   const int D = g.D, s = g.s;
   const long long gw = (long long)blockIdx.x * kMxWarps + warp;
   const long long tile = gw % g.tiles, part = gw / g.tiles;
@@ -88,7 +104,6 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
   const long long r0 = active ? g.R * part / g.parts : 0;
   const long long r1 = active ? g.R * (part + 1) / g.parts : 0;
   const long long cbase = tile * 32 * J + lane;  // column of slot j: cbase + 32 j
-  const unsigned long long* P = reinterpret_cast<const unsigned long long*>(p);
 
   // ---- lane state
   long long cs[J];                      // column sums (fixed point, the window)
@@ -242,21 +257,69 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
       wrow = 0;
     }
   };
-  auto load = [&](unsigned long long (&v)[J], long long r) {
-    const unsigned long long* rowp = P + r * g.C + cbase;
-#pragma unroll
-    for (int j = 0; j < J; ++j) v[j] = colok[j] ? __ldcs(rowp + 32 * j) : 0ull;
+  // ---- staged rows: lane 0 copies each row's tile segment into one of the warp's NS stages
+  // with a bulk copy (widened to 16-byte bounds; completion on the stage's mbarrier), so
+  // NS - 1 rows are in flight while one is summed
+  unsigned char* stages = dsm + (size_t)warp * kMxStages * kMxStageBytes;
+  const long long c0 = tile * 32 * J;                     // first column of the tile
+  const long long ncols = g.C - c0 < 32 * J ? g.C - c0 : 32 * J;
+  const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
+  auto seg_start = [&](long long r) { return pb + (r * g.C + c0) * 8; };
+  auto issue = [&](long long r, int q) {
+    const unsigned long long a = reinterpret_cast<unsigned long long>(seg_start(r));
+    const unsigned long long a16 = a & ~15ull, e16 = (a + 8 * ncols + 15) & ~15ull;
+    const unsigned nb = (unsigned)(e16 - a16);
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp][q]);
+    // this lane's earlier reads of the stage (generic proxy) come before the async write
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nb) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            (unsigned)__cvta_generic_to_shared(stages + q * kMxStageBytes)),
+        "l"(a16), "r"(nb), "r"(bar)
+        : "memory");
   };
-
+  unsigned phase = 0;          // parity of the current use of each stage
+  long long issued = r0;       // next row to stage
+  bool timed_out = false;
   if (r1 > r0) {
-    unsigned long long va[J], vb[J];
-    load(va, r0);
-    for (long long r = r0; r < r1; r += 2) {
-      if (r + 1 < r1) load(vb, r + 1);
-      row(va);
-      if (r + 1 >= r1) break;
-      if (r + 2 < r1) load(va, r + 2);
-      row(vb);
+    if (lane == 0)
+      for (int q = 0; q < kMxStages && issued < r1; ++q) issue(issued++, q);
+    else
+      issued = r0 + (r1 - r0 < kMxStages ? r1 - r0 : kMxStages);
+    int q = 0;
+    long long r = r0;
+    for (; r < r1; ++r) {
+      const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp][q]);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, (phase >> q) & 1u, kWaitLimit));
+      if (!ok) {  // the copy did not land: record it and stop (results are not to be used)
+        if (lane == 0) atomicExch(&g_mx_flag, 1);
+        timed_out = true;
+        break;
+      }
+      phase ^= 1u << q;
+      const unsigned char* buf = stages + q * kMxStageBytes +
+                                 (reinterpret_cast<unsigned long long>(seg_start(r)) & 15ull);
+      unsigned long long v[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        v[j] = colok[j] ? *reinterpret_cast<const unsigned long long*>(buf + 8 * (lane + 32 * j)) : 0ull;
+      __syncwarp();
+      if (issued < r1) {
+        if (lane == 0) issue(issued, q);
+        ++issued;
+      }
+      row(v);
+      if (++q == kMxStages) q = 0;
+    }
+    if (timed_out) {
+      // rows r .. issued-1 may still be in flight into this warp's stages (each stage holds
+      // at most one of them): wait for them, bounded, before the CTA's shared memory goes
+      for (long long x = r; x < issued; ++x) {
+        const int k = (int)((x - r0) % kMxStages);
+        const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp][k]);
+        mbar_wait_bounded(bar, (phase >> k) & 1u, kWaitLimit);
+      }
     }
     end_window();
   }
@@ -306,5 +369,13 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
 }  // namespace
 
 const void* moment_mx64_kernel_ptr() { return reinterpret_cast<const void*>(&moment_mx64_kernel<kMxJ>); }
+
+void mx_read_device_flag(int* flag) {
+  int v = 0;
+  cudaMemcpyFromSymbol(&v, g_mx_flag, sizeof(int));
+  const int zero = 0;
+  cudaMemcpyToSymbol(g_mx_flag, &zero, sizeof(int));
+  *flag = v;
+}
 
 }  // namespace triot
