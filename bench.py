@@ -671,7 +671,11 @@ def profile_op(args):
         for _ in range(n):
             triot.triot_moment_product([x8, y8], out=out, workspace=ws)
     else:
-        if args.profile_op == "moment_f32_d24":
+        if args.profile_op == "moment_f64_d8":
+            # the f64 d=8 step's moment: p = x / sum(x), x of shape 9^8, U(0,1)
+            c8 = synth.config_f64_d8()
+            p = torch.from_numpy(synth.normalise(c8.x_values()).reshape(c8.xshape)).to(dev)
+        elif args.profile_op == "moment_f32_d24":
             # the f32 d=24 workload's moment: x of shape (2,)*24, U(0,1)
             c = synth.config_f32_d24()
             p = torch.from_numpy(c.x_values().astype(np.float32).reshape(c.xshape)).to(dev)
@@ -706,7 +710,7 @@ def main():
     ap.add_argument("--autotune", default="", help="autotune the three ops and save the cache here")
     ap.add_argument("--no-tune-file", action="store_true", help="ignore the committed tuning file")
     ap.add_argument("--profile-op", default="",
-                    choices=["", "moment_product_f64_d8", "moment_f32_d24", "moment_bf16_blocks16"],
+                    choices=["", "moment_product_f64_d8", "moment_f64_d8", "moment_f32_d24", "moment_bf16_blocks16"],
                     help="only run one op a few times (the command the ncu summaries capture)")
     args = ap.parse_args()
     if args.profile_op:

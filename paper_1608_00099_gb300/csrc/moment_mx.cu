@@ -82,6 +82,41 @@ __device__ __noinline__ void mx_special(const MxGeom& g, double v, const uint32_
   sp[g.D] += v;
 }
 
+// General conversion of a lane's J elements of one row at window exponent EW (at least the
+// exponent of every finite element): signed, zero, subnormal and tiny values exactly; a
+// non-finite element gives 0 and sets its bit in the returned mask.  Out of line, so that
+// the hot loop stays small: rows of positive normal values never come here.
+template <int J>
+__device__ __noinline__ unsigned mx_convert_general(const unsigned long long* v, int EW, long long* c) {
+  unsigned spec = 0;
+  for (int j = 0; j < J; ++j) {
+    const unsigned long long b = v[j];
+    const uint32_t ef = (uint32_t)(b >> 32) & 0x7FF00000u;
+    if (ef == 0x7FF00000u) {
+      spec |= 1u << j;
+      c[j] = 0;
+      continue;
+    }
+    const int e = (int)((ef > 0x00100000u ? ef : 0x00100000u) >> 20);
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | (ef ? 0x0010000000000000ull : 0ull);
+    const long long x = (long long)shr_clamp(m, (uint32_t)(EW - e));
+    c[j] = (b >> 63) ? -x : x;
+  }
+  return spec;
+}
+
+// the largest biased exponent of the finite elements among v[0 .. J-1] (subnormals and zeros
+// count as 1), 0 when all are non-finite
+template <int J>
+__device__ __noinline__ int mx_row_emax(const unsigned long long* v) {
+  int emax = 0;
+  for (int j = 0; j < J; ++j) {
+    const uint32_t ef = (uint32_t)(v[j] >> 32) & 0x7FF00000u;
+    if (ef != 0x7FF00000u) emax = max(emax, (int)((ef > 0x00100000u ? ef : 0x00100000u) >> 20));
+  }
+  return emax;
+}
+
 template <int J>
 __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
     const __grid_constant__ MxGeom g, const double* __restrict__ p, double* __restrict__ partial) {
@@ -129,9 +164,9 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
     for (int i = 0; i + 1 < s; ++i) td[i] = dg[i];
     t1 = dg[s - 1];
   }
-  bool colok[J];
+  uint32_t colok = 0;  // bit j: column slot j lies inside the tensor
 #pragma unroll
-  for (int j = 0; j < J; ++j) colok[j] = cbase + 32 * j < g.C;
+  for (int j = 0; j < J; ++j) colok |= (cbase + 32 * j < g.C ? 1u : 0u) << j;
 
   auto rebase = [&](int e_new) {
     if (EW != 0) {
@@ -187,7 +222,7 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
         __int128 acc = 0;
 #pragma unroll
         for (int j = 0; j < J; ++j)
-          if (colok[j]) mac64x32(acc, cs[j], mx_col_digit(g, (uint32_t)(cbase + 32 * j), a));
+          if (colok >> j & 1u) mac64x32(acc, cs[j], mx_col_digit(g, (uint32_t)(cbase + 32 * j), a));
         Ad[a] += fixed_to_double(acc, sc);
       }
     }
@@ -200,13 +235,31 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
   // one row: v[j] holds the bits of column slot j (0 where the column is outside C)
   int wrow = 0;
   auto row = [&](const unsigned long long (&v)[J]) {
-    uint32_t hmax = 0;
+    uint32_t hmax = 0, hmin = 0xFFFFFFFFu;
 #pragma unroll
-    for (int j = 0; j < J; ++j) hmax = max(hmax, (uint32_t)(v[j] >> 32));
+    for (int j = 0; j < J; ++j) {
+      const uint32_t hi = (uint32_t)(v[j] >> 32);
+      hmax = max(hmax, hi);
+      hmin = min(hmin, hi);
+    }
+    // no new exponent and positive, finite values everywhere in the warp's row
+    const bool steady = hmax < 0x7FF00000u && (int)(hmax >> 20) <= EW;
     long long rp = 0;
-    // positive, finite, no new exponent, and a window exponent that turns zeros and
-    // subnormals into 0 by itself: the lean conversion
-    if (hmax < 0x7FF00000u && (int)(hmax >> 20) <= EW && EW >= 54) {
+    if (__all_sync(0xffffffffu, steady && hmin >= 0x00100000u && EW - (int)(hmin >> 20) < 32)) {
+      // normal values within 32 binades of the window exponent: 32-bit funnel shifts
+      const uint32_t ec = (uint32_t)EW;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const uint32_t hi = (uint32_t)(v[j] >> 32), lo = (uint32_t)v[j];
+        const uint32_t sh = ec - (hi >> 20);
+        const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
+        const long long c = (long long)(((unsigned long long)(mh >> sh) << 32) | __funnelshift_r(lo, mh, sh));
+        cs[j] += c;
+        rp += c;
+      }
+    } else if (__all_sync(0xffffffffu, steady && EW >= 54)) {
+      // zeros, subnormals and tiny values too (a window exponent of 54 or more sends them to
+      // 0 or their exact fixed-point value): one clamped 64-bit shift
       const uint32_t ec = (uint32_t)EW;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
@@ -217,33 +270,25 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
         rp += c;
       }
     } else {
-      // the row's largest finite exponent first, so that the whole row converts at one scale
-      int emax = 0;
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const uint32_t ef = (uint32_t)(v[j] >> 32) & 0x7FF00000u;
-        if (ef != 0x7FF00000u) emax = max(emax, (int)((ef > 0x00100000u ? ef : 0x00100000u) >> 20));
-      }
+      // anything else: the row's largest finite exponent first, so that the whole row
+      // converts at one scale, then the general conversion out of line
+      const int emax = mx_row_emax<J>(v);
       if (emax > EW) rebase(emax);
+      long long c[J];
+      const unsigned spec = mx_convert_general<J>(v, EW, c);
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        const unsigned long long b = v[j];
-        const uint32_t hi = (uint32_t)(b >> 32);
-        const uint32_t ef = hi & 0x7FF00000u;
-        if (ef == 0x7FF00000u) {
-          if (!special) {
-            for (int i = 0; i <= D; ++i) sp[i] = 0.0;
-            special = true;
-          }
-          mx_special(g, __longlong_as_double((long long)b), td, t1, (uint32_t)(cbase + 32 * j), sp);
-          continue;
+        cs[j] += c[j];
+        rp += c[j];
+      }
+      if (spec) {
+        if (!special) {
+          for (int i = 0; i <= D; ++i) sp[i] = 0.0;
+          special = true;
         }
-        const int e = (int)((ef > 0x00100000u ? ef : 0x00100000u) >> 20);
-        const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | (ef ? 0x0010000000000000ull : 0ull);
-        long long c = (long long)shr_clamp(m, (uint32_t)(EW - e));
-        if (hi >> 31) c = -c;
-        cs[j] += c;
-        rp += c;
+        for (int j = 0; j < J; ++j)
+          if (spec >> j & 1u)
+            mx_special(g, __longlong_as_double((long long)v[j]), td, t1, (uint32_t)(cbase + 32 * j), sp);
       }
     }
     mac64x32(S1, rp, t1);
@@ -263,6 +308,7 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
   unsigned char* stages = dsm + (size_t)warp * kMxStages * kMxStageBytes;
   const long long c0 = tile * 32 * J;                     // first column of the tile
   const long long ncols = g.C - c0 < 32 * J ? g.C - c0 : 32 * J;
+  const bool full_tile = ncols == 32 * J;
   const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
   auto seg_start = [&](long long r) { return pb + (r * g.C + c0) * 8; };
   auto issue = [&](long long r, int q) {
@@ -301,9 +347,14 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
       const unsigned char* buf = stages + q * kMxStageBytes +
                                  (reinterpret_cast<unsigned long long>(seg_start(r)) & 15ull);
       unsigned long long v[J];
+      if (full_tile) {
 #pragma unroll
-      for (int j = 0; j < J; ++j)
-        v[j] = colok[j] ? *reinterpret_cast<const unsigned long long*>(buf + 8 * (lane + 32 * j)) : 0ull;
+        for (int j = 0; j < J; ++j) v[j] = *reinterpret_cast<const unsigned long long*>(buf + 8 * (lane + 32 * j));
+      } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          v[j] = (colok >> j & 1u) ? *reinterpret_cast<const unsigned long long*>(buf + 8 * (lane + 32 * j)) : 0ull;
+      }
       __syncwarp();
       if (issued < r1) {
         if (lane == 0) issue(issued, q);
@@ -356,6 +407,7 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
     }
     if (lane == 0) wsum[warp][slot] = fixed_to_double(x, ew - 1139);
   };
+#pragma unroll 1
   for (int i = 0; i <= D; ++i) reduce_out(special ? Ad[i] + sp[i] : Ad[i], i);
   __syncthreads();
   if (threadIdx.x <= D) {
