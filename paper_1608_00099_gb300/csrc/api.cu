@@ -150,7 +150,7 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
     // the marginal split when the axes give good rows and columns
     const void* fmx = moment_mx64_kernel_ptr();
     int occ = 1;
-    if ((st = moment_occupancy(fmx, kMxWarps * 32, kMxDynSmem, kMxDynSmem, occ))) return st;
+    if ((st = moment_occupancy(fmx, kMxWarps * 32, 0, 0, occ))) return st;
     const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
     if (plan_moment_mx(c, rank, (long long)dev.sms * cps * kMxWarps, L)) return TRIOT_OK;
   }
@@ -190,7 +190,7 @@ int launch_moment(const MomentLaunch& L, int dtype, const void* p, double* out, 
   if (L.kind == MOMENT_KIND_MX) {
     double* part = static_cast<double*>(ws);
     void* args[] = {(void*)&L.mx, (void*)&p, (void*)&part};
-    e = cudaLaunchKernel(moment_mx64_kernel_ptr(), dim3(L.grid), dim3(L.warps * 32), args, kMxDynSmem, stream);
+    e = cudaLaunchKernel(moment_mx64_kernel_ptr(), dim3(L.grid), dim3(L.warps * 32), args, 0, stream);
     if (e != cudaSuccess) return cuda_fail(e, "moment kernel launch");
   } else if (!L.empty) {
     const void* fn = moment_kernel_ptr(dtype, L.g.D, L.g.m, L.g.B);
@@ -334,14 +334,13 @@ int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q
 int triot_device_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-  int flag = 0, flag2 = 0, flag3 = 0, flag4 = 0, flag5 = 0, flag6 = 0;
-  mx_read_device_flag(&flag6);
+  int flag = 0, flag2 = 0, flag3 = 0, flag4 = 0, flag5 = 0;
   st_read_device_flag(&flag);
   b64_read_device_flag(&flag2);
   b32_read_device_flag(&flag3);
   wb_read_device_flag(&flag4);
   selftest_read_device_flag(&flag5);
-  return (flag || flag2 || flag3 || flag4 || flag5 || flag6) ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped")
+  return (flag || flag2 || flag3 || flag4 || flag5) ? fail(TRIOT_ERR_DEVICE, "a device-side guard tripped")
                                                     : ok();
 }
 

@@ -24,7 +24,6 @@ void wb_read_device_flag(int* flag);
 const void* combine_kernel_ptr();
 // f64 moment by marginals (rows x columns split)
 const void* moment_mx64_kernel_ptr();
-void mx_read_device_flag(int* flag);
 // moment of a product of tensors: one kernel per dtype and tensor count (1..4)
 const void* moment_prod_kernel_ptr(int dtype, int ntensors);
 }  // namespace triot

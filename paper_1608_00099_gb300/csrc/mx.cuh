@@ -5,15 +5,11 @@
 
 namespace triot {
 
-constexpr int kMxWarps = 8;      // warps per CTA
+constexpr int kMxWarps = 12;     // warps per CTA
 constexpr int kMxMinCtas = 1;    // resident CTAs per SM the register budget is sized for
-constexpr int kMxJ = 16;         // columns per lane: a warp tile is 32 * kMxJ columns
+constexpr int kMxJ = 8;          // columns per lane: a warp tile is 32 * kMxJ columns
 constexpr int kMxWindow = 1023;  // rows a lane sums in one fixed-point window (|c| < 2^53)
 constexpr int kMxMaxGrid = 16384;  // CTAs (partial vectors) of one launch at most
-constexpr int kMxStages = 3;     // staged rows per warp
-// one stage: a row's tile segment (32 * kMxJ doubles) widened to 16-byte bounds
-constexpr int kMxStageBytes = 32 * kMxJ * 8 + 16;
-constexpr int kMxDynSmem = kMxWarps * kMxStages * kMxStageBytes;
 
 struct MxGeom {
   int D;                         // effective rank
