@@ -146,13 +146,22 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
   DeviceInfo dev;
   if ((st = device_info(dev))) return st;
   TuneCfg t = force ? *force : tune_lookup(TRIOT_OP_MOMENT, dtype, c);
-  if (dtype == DT_F64) {
-    // the marginal split when the axes give good rows and columns
-    const void* fmx = moment_mx64_kernel_ptr();
+  {
+    // the marginal split (rows x columns) when the axes give good rows and columns
+    const bool f64 = dtype == DT_F64;
+    const void* fmx = f64 ? moment_mx64_kernel_ptr() : moment_mx32_kernel_ptr(dtype, 2);
+    const int nw = f64 ? kMxWarps : kMx32Warps;
     int occ = 1;
-    if ((st = moment_occupancy(fmx, kMxWarps * 32, 0, 0, occ))) return st;
+    if ((st = moment_occupancy(fmx, nw * 32, 0, 0, occ))) return st;
     const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
-    if (plan_moment_mx(c, rank, (long long)dev.sms * cps * kMxWarps, L)) return TRIOT_OK;
+    // float storage: only large tensors whose rows can be read 16 bytes at a time (the
+    // per-CTA column pass and the row-side set-up need enough rows per warp to pay off;
+    // smaller tensors are latency-bound and the block kernels below serve them better)
+    const bool eligible = f64 || c.total >= kMx32MinElems;
+    if (eligible && plan_moment_mx(c, rank, dtype_size(dtype), p, (long long)dev.sms * cps * nw, L) &&
+        (f64 || (L.mx.C * dtype_size(dtype)) % 16 == 0))
+      return TRIOT_OK;
+    L = MomentLaunch();
   }
   const int m = moment_block_axes(c, dtype);
   int B = 1;
@@ -190,7 +199,8 @@ int launch_moment(const MomentLaunch& L, int dtype, const void* p, double* out, 
   if (L.kind == MOMENT_KIND_MX) {
     double* part = static_cast<double*>(ws);
     void* args[] = {(void*)&L.mx, (void*)&p, (void*)&part};
-    e = cudaLaunchKernel(moment_mx64_kernel_ptr(), dim3(L.grid), dim3(L.warps * 32), args, 0, stream);
+    const void* fn = dtype == DT_F64 ? moment_mx64_kernel_ptr() : moment_mx32_kernel_ptr(dtype, L.mx.V);
+    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.warps * 32), args, 0, stream);
     if (e != cudaSuccess) return cuda_fail(e, "moment kernel launch");
   } else if (!L.empty) {
     const void* fn = moment_kernel_ptr(dtype, L.g.D, L.g.m, L.g.B);

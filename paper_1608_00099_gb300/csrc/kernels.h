@@ -24,6 +24,8 @@ void wb_read_device_flag(int* flag);
 const void* combine_kernel_ptr();
 // f64 moment by marginals (rows x columns split)
 const void* moment_mx64_kernel_ptr();
+// float storage by marginals: V = elements per vector load (1: single-element loads)
+const void* moment_mx32_kernel_ptr(int dtype, int V);
 // moment of a product of tensors: one kernel per dtype and tensor count (1..4)
 const void* moment_prod_kernel_ptr(int dtype, int ntensors);
 }  // namespace triot

@@ -13,15 +13,26 @@ constexpr int kMxMaxGrid = 16384;  // CTAs (partial vectors) of one launch at mo
 
 struct MxGeom {
   int D;                         // effective rank
+  int V;                         // float kernel: elements per vector load (1: scalar loads)
+  int W;                         // columns of a warp tile
   int s;                         // row axes 0 .. s-1, column axes s .. D-1 (1 <= s < D)
   long long R;                   // rows (< 2^31)
   long long C;                   // columns (< 2^31)
-  long long tiles;               // column tiles of 32 * kMxJ columns
+  long long tiles;               // column tiles of W columns
   long long parts;               // row ranges per tile (one warp each)
   int win;                       // rows per fixed-point window
   int r32;                       // R < 2^32: 32-bit row decode
   long long ext[kMaxRank];       // extents (axis order, outermost first)
   FastDiv div[kMaxRank];
 };
+
+// float storage (f32, bf16, f16), accumulated in f32: a lane holds kMx32J elements per
+// row, as vectors of V = 16 bytes / element size when rows are 16-byte aligned (else V = 1);
+// a warp tile is 32 * kMx32J columns; plain f32 sums of at most kMx32Window rows
+constexpr int kMx32Warps = 8;
+constexpr int kMx32MinCtas = 2;
+constexpr int kMx32J = 16;       // elements per lane and row
+constexpr int kMx32Window = 64;  // rows per f32 window
+constexpr long long kMx32MinElems = 1ll << 25;  // float tensors this large or larger
 
 }  // namespace triot

@@ -55,7 +55,9 @@ struct MomentLaunch {
 enum { MOMENT_KIND_ROWS_BLOCKS = 0, MOMENT_KIND_MX = 1 };
 // The marginal split of a f64 moment (moment_mx.cu): false when no split of the canonical
 // axes gives rows and columns the kernel can use well.  `target_warps` = warps of a full GPU.
-bool plan_moment_mx(const Canon& c, int rank, long long target_warps, MomentLaunch& L);
+// (es: element size; p: the data, whose alignment decides vector loads for float storage)
+bool plan_moment_mx(const Canon& c, int rank, int es, const void* p, long long target_warps,
+                    MomentLaunch& L);
 // `occ` = resident CTAs per SM of the chosen kernel (from the occupancy calculator).
 void plan_moment(const Canon& c, int rank, int es, int m, const void* p, const TuneCfg& t,
                  const DeviceInfo& dev, int occ, MomentLaunch& L);

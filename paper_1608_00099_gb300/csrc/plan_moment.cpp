@@ -114,9 +114,20 @@ int moment_block_axes(const Canon& c, int dtype) {
   return axes(16, b);
 }
 
-bool plan_moment_mx(const Canon& c, int rank, long long target_warps, MomentLaunch& L) {
+bool plan_moment_mx(const Canon& c, int rank, int es, const void* p, long long target_warps,
+                    MomentLaunch& L) {
   if (c.empty || c.D < 2) return false;
-  constexpr long long W = 32 * kMxJ;  // columns of a warp tile
+  // columns of a warp tile: f64 32 * kMxJ; float storage 32 * kMx32J (vector loads of V
+  // elements when every row starts on a 16-byte boundary, else V = 1)
+  auto tile_width = [&](long long C, int& V) -> long long {
+    if (es == 8) {
+      V = 1;
+      return 32ll * kMxJ;
+    }
+    const bool vec = (reinterpret_cast<uintptr_t>(p) % 16) == 0 && (C * es) % 16 == 0;
+    V = vec ? 16 / es : 1;
+    return 32ll * kMx32J;
+  };
   // split after axis s-1: the best use of the tiles' columns, then columns near 2^12
   int best_s = 0;
   double best_score = -1.0;
@@ -124,6 +135,8 @@ bool plan_moment_mx(const Canon& c, int rank, long long target_warps, MomentLaun
     long long C = 1, R = 1;
     for (int a = s; a < c.D; ++a) C *= c.ext[a];
     for (int a = 0; a < s; ++a) R *= c.ext[a];
+    int V = 1;
+    const long long W = tile_width(C, V);
     if (C >= (1ll << 31) || R >= (1ll << 31) || C < W / 2) continue;
     const long long tiles = (C + W - 1) / W;
     const double eff = double(C) / double(tiles * W);
@@ -150,18 +163,29 @@ bool plan_moment_mx(const Canon& c, int rank, long long target_warps, MomentLaun
     g.div[i] = make_fastdiv((uint32_t)c.ext[i]);
   }
   g.r32 = g.R < (1ll << 32);
-  g.tiles = (g.C + W - 1) / W;
-  // one warp per (tile, row range): enough ranges to fill the GPU, whole warps per CTA
-  long long parts = std::max(1ll, std::min(g.R, target_warps / g.tiles));
-  g.parts = parts;
-  const long long rows_per_warp = (g.R + parts - 1) / parts;
-  g.win = (int)std::min<long long>(kMxWindow, std::max(1ll, rows_per_warp));
-  const long long warps = g.tiles * parts;
-  const long long grid = (warps + kMxWarps - 1) / kMxWarps;
+  g.W = (int)tile_width(g.C, g.V);
+  g.tiles = (g.C + g.W - 1) / g.W;
+  const int nw = es == 8 ? kMxWarps : kMx32Warps;
+  long long grid;
+  if (es == 8) {
+    // one warp per (tile, row range): enough ranges to fill the GPU, whole warps per CTA
+    const long long parts = std::max(1ll, std::min(g.R, target_warps / g.tiles));
+    g.parts = parts;
+    const long long rows_per_warp = (g.R + parts - 1) / parts;
+    g.win = (int)std::min<long long>(kMxWindow, std::max(1ll, rows_per_warp));
+    grid = (g.tiles * parts + nw - 1) / nw;
+  } else {
+    // one CTA per (tile, row range), its warps splitting the range: the CTA's warps share
+    // their tile's columns, so the column axes' moments are formed once per CTA
+    const long long parts = std::max(1ll, std::min((g.R + nw - 1) / nw, target_warps / nw / g.tiles));
+    g.parts = parts;
+    g.win = kMx32Window;
+    grid = g.tiles * parts;
+  }
   if (grid > kMxMaxGrid) return false;
   L.kind = MOMENT_KIND_MX;
   L.grid = (int)grid;
-  L.warps = kMxWarps;
+  L.warps = nw;
   L.smem = 0;
   L.empty = false;
   // the row/block geometry is unused, but the effective rank must be right for the

@@ -128,3 +128,32 @@ def test_mx_many_windows_separable_closed_form(tr):
         assert list(got) == ref
     finally:
         tr.triot_tune_clear()
+
+
+# float storage takes the marginal kernel for large tensors whose rows are 16-byte multiples
+MX32_CASES = [
+    ("f32", (4,) * 13, False),             # 67M elements, vector loads
+    ("f32", (4,) * 13, True),              # the same from a pointer 4 bytes past a 16-byte bound
+    ("bf16", (4,) * 12 + (2,), False),     # 33.5M elements, eight per vector
+    ("f16", (8, 4096, 1024), False),
+    ("bf16", (3, 5, 7, 320000), False),    # a partial last tile (320000 % 512 != 0)
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype,shape,shifted", MX32_CASES)
+def test_mx_float_moment_against_oracle(tr, dtype, shape, shifted):
+    from test_gpu_parity import TORCH, host_values, misaligned, to_dev
+    plan = tr.triot_moment_plan(shape, TORCH[dtype])
+    assert plan["kernel"] == "marginals", plan
+    n = int(np.prod(shape))
+    ph = host_values(n, dtype, 4100 + len(shape), law="uniform")
+    if shifted:
+        p = misaligned(shape, dtype)
+        p.copy_(to_dev(ph, dtype, shape))
+    else:
+        p = to_dev(ph, dtype, shape)
+    got = tr.triot_moment(p).cpu().numpy()
+    ref = orc.moment(ph, shape, dtype, nthreads=16)
+    check_moment(got, ref, np.abs(ref), 1e-5)   # p >= 0: the scale is the value itself
+    assert tr.triot_moment(p).cpu().numpy().tobytes() == got.tobytes()
