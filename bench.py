@@ -244,6 +244,9 @@ def run_ours(args, rank, world, local, dist):
         result["workloads"] = run_extra_workloads(args, triot, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args, cfg, xh, yph, ph)
+        if PRECISION_OUTPUTS and "workloads" in result:
+            for name, e in precision_errors(synth).items():
+                result["workloads"][f"precision_{name}"]["errors_vs_oracle"] = e
     return result
 
 
@@ -484,9 +487,9 @@ def run_extra_workloads(args, triot, synth, dev, stream):
     pc = synth.config_precision()
     I = tuple(min(a, b) for a, b in zip(pc.pshape, pc.qshape))
     nI = int(np.prod(I))
-    tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f64": torch.float64}
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32, "f64": torch.float64}
     for name, dt in tdt.items():
-        es = 8 if name == "f64" else 2
+        es = {"f64": 8, "f32": 4}.get(name, 2)
         pt = synth.to_storage(pc.p64, name).reshape(pc.pshape)
         qt = synth.to_storage(pc.q64, name).reshape(pc.qshape)
         per = es * (pt.numel() + qt.numel() + nI)
@@ -509,6 +512,12 @@ def run_extra_workloads(args, triot, synth, dev, stream):
         ms = time_op(lambda k, st: triot.triot_moment_product([P[k % ncopy], Q[k % ncopy]], out=out,
                                                               workspace=wsp, stream=st), 3 * ncopy, stream)
         r["moment_product"] = op_entry(2 * es * nI, ms, peak, nI)
+        # one untimed pass whose results the CPU leg checks against the oracle
+        triot.triot_crop(R[0], P[0], stream=stream)
+        triot.triot_product(Q[0], R[0], stream=stream)
+        m0 = triot.triot_moment(R[0], stream=stream)
+        torch.cuda.synchronize()
+        PRECISION_OUTPUTS[name] = (R[0].cpu().contiguous(), m0.cpu().numpy().copy())
         res[f"precision_{name}"] = r
         del P, Q, R
     torch.cuda.empty_cache()
@@ -606,6 +615,59 @@ def oracle_step(cfg, xh, yph, ph, nt, slabs=None):
     nI = int(np.prod([min(a, b) for a, b in zip(xs, ps)]))
     nbytes = 8 * (int(np.prod(xs)) + int(np.prod(es))) + 24 * nI + 8 * int(np.prod(xs))
     return nbytes, dt
+
+
+# outputs of the precision workload's GPU pass (dtype -> (r, moments)), checked by the CPU leg
+PRECISION_OUTPUTS = {}
+# error bounds the precision workload is held to: the product relative to the exact product
+# of the rounded inputs (where that is a normal number of the format; half a subnormal step
+# elsewhere), the moment relative to sum |r| t_i against the FP64 oracle
+PRODUCT_BOUND = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11, "f32": 2.0 ** -24, "f64": 2.0 ** -53}
+MOMENT_BOUND = {"bf16": 1e-5, "f16": 1e-5, "f32": 1e-5, "f64": 1e-12}
+NONNORMAL_BOUND = {"bf16": 2.0 ** -134, "f16": 2.0 ** -25, "f32": 2.0 ** -150, "f64": 2.0 ** -1075}
+
+
+def precision_errors(synth):
+    """Per-result errors of the precision workload (d = 10, extents 3..7) against the oracle:
+    the product r = crop(p) * q element by element, and the moment of r per component."""
+    from oracle import oracle as orc
+    pc = synth.config_precision()
+    I = tuple(min(a, b) for a, b in zip(pc.pshape, pc.qshape))
+    tiny = {"bf16": 2.0 ** -126, "f16": 2.0 ** -14, "f32": 2.0 ** -126, "f64": 2.0 ** -1022}
+    out = {}
+    for name, (rt, mg) in PRECISION_OUTPUTS.items():
+        # the very inputs the GPU pass used (rounded by synth.to_storage)
+        def bits(a64):
+            t = synth.to_storage(a64, name).contiguous()
+            return t.view(torch_int16()).numpy().view(np.uint16).reshape(-1) if name in ("bf16", "f16") \
+                else t.numpy().reshape(-1)
+        ph, qh = bits(pc.p64), bits(pc.q64)
+        rp = orc.crop(ph, I, pc.pshape, name)
+        rq = orc.crop(qh, I, pc.qshape, name)
+        ref = orc.product(qh, pc.qshape, rp, I, name)
+        got = rt.view(torch_int16()).numpy().view(np.uint16).reshape(-1) if name in ("bf16", "f16") \
+            else rt.numpy().reshape(-1)
+        exact = orc.to_f64(rp, name) * orc.to_f64(rq, name)
+        g64 = orc.to_f64(got, name)
+        normal = np.abs(exact) >= tiny[name]
+        rel = np.abs(g64[normal] - exact[normal]) / np.abs(exact[normal]) if normal.any() else np.zeros(1)
+        absn = np.abs(g64[~normal] - exact[~normal]) if (~normal).any() else np.zeros(1)
+        mref = orc.moment(ref, I, name)
+        scale = np.abs(orc.moment(np.abs(orc.to_f64(ref, name)), I, "f64"))
+        merr = np.abs(mg - mref) / np.maximum(scale, 1e-300)
+        out[name] = {"product_bit_exact_vs_oracle": bool(got.tobytes() == ref.tobytes()),
+                     "max_rel_err_product": float(rel.max()), "product_normal_results": int(normal.sum()),
+                     "max_abs_err_product_nonnormal": float(absn.max()),
+                     "product_bound_rel": PRODUCT_BOUND[name], "product_bound_abs_nonnormal": NONNORMAL_BOUND[name],
+                     "max_rel_err_moment": float(merr.max()), "moment_bound_rel": MOMENT_BOUND[name],
+                     "within_bounds": bool(rel.max() <= PRODUCT_BOUND[name] and absn.max() <= NONNORMAL_BOUND[name]
+                                           and merr.max() <= MOMENT_BOUND[name])}
+    return out
+
+
+def torch_int16():
+    import torch
+    return torch.int16
 
 
 def cpu_baseline(args, cfg, xh, yph, ph):

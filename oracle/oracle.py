@@ -56,6 +56,8 @@ def load(path: str):
     L.oracle_moment_product.argtypes = [C.c_int, C.c_uint, C.c_uint, _u64p, C.POINTER(C.c_void_p),
                                         C.POINTER(C.c_double)]
     L.oracle_convolve_f64.argtypes = [C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, C.c_void_p]
+    L.oracle_nonzero_bbox.argtypes = [C.c_int, C.c_uint, C.c_uint, _u64p, C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_int64)]
     return L
 
 
@@ -268,6 +270,22 @@ def moment_product(tensors, shapes, dtype: str) -> np.ndarray:
     out = np.zeros(d + 1, dtype=np.float64)
     lib().oracle_moment_product(DTYPES[dtype], d, len(flat), _p(allshapes), ptrs,
                                 out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def nonzero_bbox(tensors, shapes, dtype: str) -> np.ndarray:
+    """Nonzero bounding box of the product of the tensors over the intersection of their
+    shapes: int64 [lo_0, hi_0, ..., lo_{d-1}, hi_{d-1}, count] (empty: lo 0, hi -1)."""
+    d = len(shapes[0])
+    assert all(len(s) == d for s in shapes) and len(tensors) == len(shapes) >= 1
+    flat = [np.ascontiguousarray(x).reshape(-1) for x in tensors]
+    for x, s in zip(flat, shapes):
+        _check(x, dtype, int(np.prod(s)))
+    allshapes = np.ascontiguousarray(np.concatenate([_shape(s) for s in shapes]))
+    ptrs = (C.c_void_p * len(flat))(*[x.ctypes.data for x in flat])
+    out = np.zeros(2 * d + 1, dtype=np.int64)
+    lib().oracle_nonzero_bbox(DTYPES[dtype], d, len(flat), _p(allshapes), ptrs,
+                              out.ctypes.data_as(C.POINTER(C.c_int64)))
     return out
 
 

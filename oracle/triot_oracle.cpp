@@ -543,6 +543,47 @@ void oracle_product_at(int dtype, unsigned dim, const u64* xshape, const void* x
 // `shapes` holds n shapes of `dim` extents each, tensor k's at shapes[k*dim].  The tuples
 // of I are walked with Algorithm 3 and each tensor is addressed by Horner's rule
 // (Algorithm 2) with its own shape; sums are Neumaier-compensated in f64.
+// The nonzero bounding box of a product of tensors (Section 2: with the tuple visible to
+// the operation, "the nonzero bounding box for the element-wise product of two tensors" is
+// a plain loop).  Walks the tuples t of the intersection I of the shapes in order
+// (Algorithm 3) and counts t when every factor x_k[t] is nonzero -- the support of the
+// product of the tensors as real functions, so no rounding is involved; NaN and infinities
+// count as nonzero, +0 and -0 do not.  out[2i] / out[2i+1]: the least and greatest t_i over
+// the counted tuples, out[2 dim]: their number; with none counted, out[2i] = 0 and
+// out[2i+1] = -1 (an empty range on every axis).
+void oracle_nonzero_bbox(int dtype, unsigned dim, unsigned n, const u64* shapes,
+                         const void* const* ptrs, int64_t* out) {
+  for (unsigned i = 0; i < dim; ++i) {
+    out[2 * i] = 0;
+    out[2 * i + 1] = -1;
+  }
+  out[2 * dim] = 0;
+  if (n == 0) return;
+  std::vector<u64> I(dim);
+  for (unsigned i = 0; i < dim; ++i) {
+    I[i] = shapes[i];
+    for (unsigned k = 1; k < n; ++k) I[i] = shapes[k * dim + i] < I[i] ? shapes[k * dim + i] : I[i];
+  }
+  const u64 count = count_of(I.data(), dim);
+  std::vector<u64> t(dim, 0);
+  int64_t found = 0;
+  for (u64 c = 0; c < count; ++c) {
+    bool nonzero = true;
+    for (unsigned k = 0; k < n && nonzero; ++k)
+      nonzero = load_as_double(ptrs[k], tuple_to_index(t.data(), shapes + k * dim, dim), dtype) != 0.0;
+    if (nonzero) {
+      for (unsigned i = 0; i < dim; ++i) {
+        const int64_t v = int64_t(t[i]);
+        if (found == 0 || v < out[2 * i]) out[2 * i] = v;
+        if (found == 0 || v > out[2 * i + 1]) out[2 * i + 1] = v;
+      }
+      ++found;
+    }
+    advance_tuple(t.data(), I.data(), dim);
+  }
+  out[2 * dim] = found;
+}
+
 void oracle_moment_product(int dtype, unsigned dim, unsigned n, const u64* shapes,
                            const void* const* ptrs, double* out) {
   for (unsigned i = 0; i <= dim; ++i) out[i] = 0.0;

@@ -59,3 +59,38 @@ def test_committed_embed_record():
     assert bench.ncu_traffic("embed_f64_d8") == rec["dram_bytes_per_launch"]
     algo = bench.step_bytes(synth.config_f64_d8())["embed"]
     assert 0.9 * algo <= rec["dram_bytes_per_launch"] <= 1.05 * algo
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "f32", "f64"])
+def test_precision_errors_report(monkeypatch, dtype):
+    """The precision workload's error report on CPU: outputs equal to the oracle's own give a
+    bit-exact product and zero moment error; a planted product error shows up."""
+    import numpy as np
+    import torch
+    from oracle import oracle as orc
+    pc = synth.config_precision()
+    I = tuple(min(a, b) for a, b in zip(pc.pshape, pc.qshape))
+
+    def bits(a64):
+        t = synth.to_storage(a64, dtype).contiguous()
+        return t.view(torch.int16).numpy().view(np.uint16).reshape(-1) if dtype in ("bf16", "f16") \
+            else t.numpy().reshape(-1)
+    ph, qh = bits(pc.p64), bits(pc.q64)
+    r = orc.product(qh, pc.qshape, orc.crop(ph, I, pc.pshape, dtype), I, dtype)
+    m = orc.moment(r, I, dtype)
+    rt = torch.from_numpy(r.view(np.int16).copy()).view({"bf16": torch.bfloat16, "f16": torch.float16}[dtype]) \
+        if dtype in ("bf16", "f16") else torch.from_numpy(r.copy())
+    monkeypatch.setattr(bench, "PRECISION_OUTPUTS", {dtype: (rt, m)})
+    e = bench.precision_errors(synth)[dtype]
+    assert e["product_bit_exact_vs_oracle"] and e["max_rel_err_moment"] == 0.0 and e["within_bounds"]
+    assert e["max_rel_err_product"] <= bench.PRODUCT_BOUND[dtype]
+    # a planted error: one result scaled by (1 + 4 bounds) is reported above the bound
+    r2 = orc.to_f64(r, dtype)
+    k = int(np.argmax(np.abs(r2)))
+    r2[k] = r2[k] * (1 + 4 * bench.PRODUCT_BOUND[dtype]) if r2[k] >= 1e-4 else 0.5  # f16 results underflow
+    bad = orc.from_f64(r2, dtype) if dtype in ("bf16", "f16") else r2.astype(r.dtype)
+    rt2 = torch.from_numpy(bad.view(np.int16).copy()).view(rt.dtype) if dtype in ("bf16", "f16") \
+        else torch.from_numpy(bad.copy())
+    monkeypatch.setattr(bench, "PRECISION_OUTPUTS", {dtype: (rt2, m)})
+    e = bench.precision_errors(synth)[dtype]
+    assert not e["product_bit_exact_vs_oracle"] and not e["within_bounds"]

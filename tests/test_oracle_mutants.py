@@ -49,6 +49,12 @@ MUTANTS = [
      "const u64 iy = tuple_to_index(t.data(), yshape, dim), iz = tuple_to_index(t.data(), zshape, dim);",
      "const u64 iy = tuple_to_index(t.data(), yshape, dim), iz = tuple_to_index(t.data(), yshape, dim);",
      [lambda o: pins.test_apply_xpyxmz_against_numpy(o, "f64", 0)]),
+    ("bounding box tests only the first factor",
+     "for (unsigned k = 0; k < n && nonzero; ++k)", "for (unsigned k = 0; k < 1 && nonzero; ++k)",
+     [lambda o: pins.test_nonzero_bbox_closed_forms(o)]),
+    ("bounding box keeps the first tuple as the upper end",
+     "if (found == 0 || v > out[2 * i + 1]) out[2 * i + 1] = v;", "if (found == 0) out[2 * i + 1] = v;",
+     [lambda o: pins.test_nonzero_bbox_closed_forms(o)]),
     ("bf16 product rounds with f16 parameters",
      "yy[iy] = uint16_t(round_to_format(exact, 8, -126, 127, 8));",
      "yy[iy] = uint16_t(round_to_format(exact, 11, -14, 15, 5));",

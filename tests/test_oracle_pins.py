@@ -591,3 +591,70 @@ def test_convolution_against_scipy(orc):
     a, b = rng.random((2 ** 5, 2 ** 3)), rng.random((2 ** 4, 2 ** 3))
     got = orc.convolve_f64(a, a.shape, b, b.shape)
     assert np.allclose(got, signal.convolve(a, b, method="direct"), rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- Section 2: nonzero bounding box
+
+def _bbox_numpy(tensors, shapes):
+    """Brute force: the indices of the nonzero entries of the factors' product over the
+    intersection, via numpy.nonzero (every factor nonzero)."""
+    I = tuple(min(s[i] for s in shapes) for i in range(len(shapes[0])))
+    nz = np.ones(I, dtype=bool)
+    for x, s in zip(tensors, shapes):
+        nz &= (x.reshape(s)[tuple(slice(0, e) for e in I)] != 0)
+    idx = np.nonzero(nz)
+    out = []
+    for a in idx:
+        out += [int(a.min()), int(a.max())] if a.size else [0, -1]
+    return out + [int(nz.sum())]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_nonzero_bbox_brute_force(orc, seed):
+    rng = np.random.default_rng(400 + seed)
+    d = int(rng.integers(1, 5))
+    n = int(rng.integers(1, 4))
+    shapes = [tuple(int(v) for v in rng.integers(1, 7, size=d)) for _ in range(n)]
+    tensors = []
+    for s in shapes:
+        x = rng.standard_normal(int(np.prod(s)))
+        x[rng.random(x.size) < 0.8] = 0.0         # mostly zero: boxes of all sizes
+        tensors.append(x)
+    assert list(orc.nonzero_bbox(tensors, shapes, "f64")) == _bbox_numpy(tensors, shapes)
+
+
+def test_nonzero_bbox_closed_forms(orc):
+    # a box-supported x times an all-ones y: the box clipped to the intersection
+    xs, ys = (9, 8, 7), (6, 10, 7)
+    x = np.zeros(xs)
+    x[2:8, 3:5, 1:7] = 1.5
+    y = np.ones(int(np.prod(ys)))
+    got = orc.nonzero_bbox([x.reshape(-1), y], [xs, ys], "f64")
+    assert list(got) == [2, 5, 3, 4, 1, 6, (6 - 2) * 2 * 6]
+    # two boxes: their intersection; disjoint boxes: empty
+    y2 = np.zeros(ys)
+    y2[4:6, 0:4, 0:3] = -2.0
+    assert list(orc.nonzero_bbox([x.reshape(-1), y2.reshape(-1)], [xs, ys], "f64")) == [4, 5, 3, 3, 1, 2, 2 * 1 * 2]
+    y3 = np.zeros(ys)
+    y3[0:2] = 1.0
+    assert list(orc.nonzero_bbox([x.reshape(-1), y3.reshape(-1)], [xs, ys], "f64")) == [0, -1] * 3 + [0]
+    # signed zeros never count; NaN and inf do; an empty intersection is empty
+    z = np.array([0.0, -0.0, np.nan, np.inf, -0.0])
+    assert list(orc.nonzero_bbox([z], [(5,)], "f64")) == [2, 3, 2]
+    assert list(orc.nonzero_bbox([np.ones(6), np.ones(0)], [(2, 3), (0, 3)], "f64")) == [0, -1, 0, -1, 0]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_nonzero_bbox_storage_types(orc, dtype):
+    rng = np.random.default_rng(9)
+    s1, s2 = (5, 6, 7), (6, 4, 8)
+    a = rng.standard_normal(int(np.prod(s1)))
+    b = rng.standard_normal(int(np.prod(s2)))
+    a[rng.random(a.size) < 0.7] = 0.0
+    b[rng.random(b.size) < 0.5] = -0.0
+    # tiny values stay nonzero in storage; products that would underflow still count
+    b[3] = 1e-30 if dtype != "f16" else 6e-8
+    conv = (lambda v: v.astype(np.float32)) if dtype == "f32" else (lambda v: orc.from_f64(v, dtype))
+    ra, rb = conv(a), conv(b)
+    want = _bbox_numpy([orc.to_f64(ra, dtype), orc.to_f64(rb, dtype)], [s1, s2])
+    assert list(orc.nonzero_bbox([ra, rb], [s1, s2], dtype)) == want
