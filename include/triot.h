@@ -241,6 +241,29 @@ int triot_moment_product(int rank, int ntensors, const int64_t* const* shapes,
                          const void* const* tensors, int dtype, double* out, void* workspace,
                          size_t workspace_bytes, void* stream);
 
+/*
+ * triot_nonzero_bbox -- the bounding box of the nonzero entries of a product of tensors
+ *   (Section 2: with the tuple visible to the operation, "the nonzero bounding box for the
+ *   element-wise product of two tensors" is a reduction over the tuples):
+ *       I        = elementwise minimum of the shapes
+ *       counted  = the tuples t of I with x_k[t] != 0 for every k (the support of the
+ *                  product as real functions: IEEE comparison with zero, so NaN and
+ *                  infinities count, +0 and -0 do not; nothing is rounded)
+ *       out[2i]  = least t_i over the counted tuples, out[2i+1] = greatest t_i (i = 0 ..
+ *                  rank-1, zero-based), out[2 rank] = the number of counted tuples
+ *   With nothing counted (or an empty I) every out[2i] = 0 and out[2i+1] = -1, count 0.
+ *   ntensors: 1 .. 4.  shapes[k]: HOST array of rank extents; tensors[k]: DEVICE data of one
+ *   dtype (dense row-major, read only).  out: DEVICE array of 2 rank + 1 int64.  workspace:
+ *   device scratch of at least triot_nonzero_bbox_workspace_size() bytes, 16-byte aligned
+ *   (its contents on entry are ignored).  Exact: min / max / count do not depend on the
+ *   order of the tuples, so results are identical from run to run.  Two kernels are
+ *   enqueued.  Errors as triot_moment_product.
+ */
+int triot_nonzero_bbox_workspace_size(int rank, int ntensors, const int64_t* const* shapes, int dtype,
+                                      size_t* bytes);
+int triot_nonzero_bbox(int rank, int ntensors, const int64_t* const* shapes, const void* const* tensors,
+                       int dtype, int64_t* out, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------ batched launch */
 
 /*

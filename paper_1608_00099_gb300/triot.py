@@ -75,6 +75,8 @@ def lib() -> C.CDLL:
             "triot_product_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
             "triot_moment_product_workspace_size": (i, [i, i, C.POINTER(_I64P), i, C.POINTER(sz)]),
             "triot_moment_product": (i, [i, i, C.POINTER(_I64P), C.POINTER(vp), i, vp, vp, sz, vp]),
+            "triot_nonzero_bbox_workspace_size": (i, [i, i, C.POINTER(_I64P), i, C.POINTER(sz)]),
+            "triot_nonzero_bbox": (i, [i, i, C.POINTER(_I64P), C.POINTER(vp), i, vp, vp, sz, vp]),
             "triot_batch_plan_create": (i, [C.POINTER(BatchDesc), i, i, i, C.POINTER(Tune), C.POINTER(vp)]),
             "triot_batch_run": (i, [vp, vp]),
             "triot_batch_run_plain": (i, [vp, vp]),
@@ -283,6 +285,36 @@ def triot_moment_product(tensors, out: torch.Tensor | None = None, workspace: to
     _check(lib().triot_moment_product(rank, len(tensors), table, ptrs, _dtype(tensors[0]), _dev(out),
                                       _dev(workspace), workspace.numel() * workspace.element_size(),
                                       _stream(stream)))
+    return out
+
+
+def triot_nonzero_bbox_workspace_size(shapes, dtype: torch.dtype) -> int:
+    n = C.c_size_t(0)
+    table, _keep = _shape_table(shapes)
+    _check(lib().triot_nonzero_bbox_workspace_size(len(shapes[0]), len(shapes), table, DTYPE_CODE[dtype],
+                                                   C.byref(n)))
+    return int(n.value)
+
+
+def triot_nonzero_bbox(tensors, out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+    """[lo_0, hi_0, .., lo_{d-1}, hi_{d-1}, count] of the nonzero entries of the tensors' product."""
+    tensors = list(tensors)
+    shapes = [tuple(t.shape) for t in tensors]
+    rank = len(shapes[0])
+    dev = tensors[0].device
+    if out is None:
+        out = torch.empty(2 * rank + 1, dtype=torch.int64, device=dev)
+    if out.dtype != torch.int64 or out.numel() < 2 * rank + 1:
+        raise TriotError(8, "out must hold 2 rank + 1 int64 values")
+    if workspace is None:
+        nb = triot_nonzero_bbox_workspace_size(shapes, tensors[0].dtype)
+        workspace = torch.empty((nb + 15) // 16 * 2, dtype=torch.int64, device=dev)
+    table, _keep = _shape_table(shapes)
+    ptrs = (C.c_void_p * len(tensors))(*[_dev(t) for t in tensors])
+    _check(lib().triot_nonzero_bbox(rank, len(tensors), table, ptrs, _dtype(tensors[0]), _dev(out),
+                                    _dev(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream(stream)))
     return out
 
 

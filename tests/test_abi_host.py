@@ -141,6 +141,14 @@ def test_bad_arguments_fail_before_any_gpu_work(tr):
     assert L.triot_moment_product(3, 2, neg, ptrs, 0, fake2, fake2, 1 << 20, None) == 2
     nbytes = C.c_size_t(0)
     assert L.triot_moment_product_workspace_size(3, 0, shp, 0, C.byref(nbytes)) == 8
+    # nonzero bounding box: tensor count, rank, dtype, shapes
+    assert L.triot_nonzero_bbox(3, 0, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 8
+    assert L.triot_nonzero_bbox(3, 5, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 8
+    assert L.triot_nonzero_bbox(25, 2, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 1
+    assert L.triot_nonzero_bbox(3, 2, shp, ptrs, 7, fake2, fake2, 1 << 20, None) == 4
+    assert L.triot_nonzero_bbox(3, 2, None, ptrs, 0, fake2, fake2, 1 << 20, None) == 3
+    assert L.triot_nonzero_bbox(3, 2, neg, ptrs, 0, fake2, fake2, 1 << 20, None) == 2
+    assert L.triot_nonzero_bbox_workspace_size(3, 2, shp, 0, None) == 3
     # convolution: f64 only, rank, shapes
     assert L.triot_convolve(3, s3, fake, s3, fake2, fake, 1, None) == 4
     assert L.triot_convolve(0, s3, fake, s3, fake2, fake, 0, None) == 1
