@@ -577,7 +577,17 @@ def run_extra_workloads(args, triot, synth, dev, stream):
     ms = time_op(lambda k, st: triot.triot_moment_product([x8, y8], out=out8, workspace=ws8, stream=st), 20, stream)
     res["moment_product_f64_d8"] = {"moment_product": op_entry(2 * 8 * n8, ms, peak, n8),
                                     "unfused_bytes": 4 * 8 * n8, "intersection": list(I8)}
-    del x8, y8
+    # nonzero bounding box of the same pair's product (Section 2), y 99.9 % zeros: both
+    # factors are read at every tuple of I (x has no zeros), 2 * 8 * |I| bytes
+    yh = c8.yprod_values()
+    yh[synth.uniform01(4242, yh.size) < 0.999] = 0.0
+    ys8 = torch.from_numpy(yh.reshape(c8.prod_shape)).to(dev)
+    bo = torch.empty(2 * len(I8) + 1, dtype=torch.int64, device=dev)
+    bws = torch.empty(triot.triot_nonzero_bbox_workspace_size([c8.xshape, c8.prod_shape], torch.float64) // 8 + 2,
+                      dtype=torch.int64, device=dev)
+    ms = time_op(lambda k, st: triot.triot_nonzero_bbox([x8, ys8], out=bo, workspace=bws, stream=st), 20, stream)
+    res["bbox_f64_d8"] = {"nonzero_bbox": op_entry(2 * 8 * n8, ms, peak, n8), "y_nonzero_fraction": 0.001}
+    del x8, y8, ys8
     torch.cuda.empty_cache()
     return res
 

@@ -56,6 +56,10 @@ def load(path: str):
     L.oracle_moment_product.argtypes = [C.c_int, C.c_uint, C.c_uint, _u64p, C.POINTER(C.c_void_p),
                                         C.POINTER(C.c_double)]
     L.oracle_convolve_f64.argtypes = [C.c_uint, _u64p, C.c_void_p, _u64p, C.c_void_p, C.c_void_p]
+    L.oracle_copy_views.argtypes = [C.c_int, C.c_uint, _u64p, _u64p, C.c_void_p, _u64p, _u64p,
+                                     C.c_void_p, _u64p]
+    L.oracle_product_views.argtypes = [C.c_int, C.c_uint, _u64p, _u64p, C.c_void_p, _u64p, _u64p,
+                                       C.c_void_p, _u64p]
     L.oracle_nonzero_bbox.argtypes = [C.c_int, C.c_uint, C.c_uint, _u64p, C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_int64)]
     return L
@@ -255,6 +259,29 @@ def product_at(x: np.ndarray, xshape, y: np.ndarray, yshape, ystart, dtype: str)
     _check(y, dtype, int(np.prod(ys)))
     lib().oracle_product_at(DTYPES[dtype], len(xs), _p(xs), _buf(x), _p(ys), _buf(y), _p(st))
     return y
+
+
+def _window_call(fn, ext, x, xshape, xstart, y, yshape, ystart, dtype):
+    e, xs, ys = _shape(ext), _shape(xshape), _shape(yshape)
+    xo, yo = _shape(xstart), _shape(ystart)
+    x = np.ascontiguousarray(x).reshape(-1)
+    y = np.ascontiguousarray(y).reshape(-1).copy()
+    _check(x, dtype, int(np.prod(xs)))
+    _check(y, dtype, int(np.prod(ys)))
+    assert all(int(a) + int(b) <= int(c) for a, b, c in zip(xo, e, xs))
+    assert all(int(a) + int(b) <= int(c) for a, b, c in zip(yo, e, ys))
+    fn(DTYPES[dtype], len(e), _p(e), _p(xs), _buf(x), _p(xo), _p(ys), _buf(y), _p(yo))
+    return y
+
+
+def copy_views(ext, x, xshape, xstart, y, yshape, ystart, dtype: str) -> np.ndarray:
+    """A copy of y with y[ystart + t] = x[xstart + t] for the tuples t of ext (Section 4)."""
+    return _window_call(lib().oracle_copy_views, ext, x, xshape, xstart, y, yshape, ystart, dtype)
+
+
+def product_views(ext, x, xshape, xstart, y, yshape, ystart, dtype: str) -> np.ndarray:
+    """A copy of y with y[ystart + t] *= x[xstart + t] for the tuples t of ext (Section 4)."""
+    return _window_call(lib().oracle_product_views, ext, x, xshape, xstart, y, yshape, ystart, dtype)
 
 
 def moment_product(tensors, shapes, dtype: str) -> np.ndarray:

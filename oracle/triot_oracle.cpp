@@ -543,6 +543,39 @@ void oracle_product_at(int dtype, unsigned dim, const u64* xshape, const void* x
 // `shapes` holds n shapes of `dim` extents each, tensor k's at shapes[k*dim].  The tuples
 // of I are walked with Algorithm 3 and each tensor is addressed by Horner's rule
 // (Algorithm 2) with its own shape; sums are Neumaier-compensated in f64.
+// Windows on both sides (Section 4: a view adds to every flat index the bias of its start
+// tuple, both computed with its container's shape; views over the intersecting support let
+// the product of two PMFs run without copies).  For every tuple t of the window extents
+// `ext`:  copy:     y[ystart + t] = x[xstart + t]
+//         product:  y[ystart + t] = y[ystart + t] * x[xstart + t]   (rounded as product)
+// The caller guarantees that both windows lie inside their containers.
+void oracle_copy_views(int dtype, unsigned dim, const u64* ext, const u64* xshape, const void* x,
+                        const u64* xstart, const u64* yshape, void* y, const u64* ystart) {
+  const size_t es = elem_size(dtype);
+  const u64 n = count_of(ext, dim);
+  if (n == 0) return;
+  const u64 xbias = tuple_to_index(xstart, xshape, dim), ybias = tuple_to_index(ystart, yshape, dim);
+  std::vector<u64> t(dim, 0);
+  for (u64 k = 0; k < n; ++k) {
+    std::memcpy(static_cast<char*>(y) + (ybias + tuple_to_index(t.data(), yshape, dim)) * es,
+                static_cast<const char*>(x) + (xbias + tuple_to_index(t.data(), xshape, dim)) * es, es);
+    advance_tuple(t.data(), ext, dim);
+  }
+}
+
+void oracle_product_views(int dtype, unsigned dim, const u64* ext, const u64* xshape, const void* x,
+                           const u64* xstart, const u64* yshape, void* y, const u64* ystart) {
+  const u64 n = count_of(ext, dim);
+  if (n == 0) return;
+  const u64 xbias = tuple_to_index(xstart, xshape, dim), ybias = tuple_to_index(ystart, yshape, dim);
+  std::vector<u64> t(dim, 0);
+  for (u64 k = 0; k < n; ++k) {
+    multiply_into(y, ybias + tuple_to_index(t.data(), yshape, dim), x,
+                  xbias + tuple_to_index(t.data(), xshape, dim), dtype);
+    advance_tuple(t.data(), ext, dim);
+  }
+}
+
 // The nonzero bounding box of a product of tensors (Section 2: with the tuple visible to
 // the operation, "the nonzero bounding box for the element-wise product of two tensors" is
 // a plain loop).  Walks the tuples t of the intersection I of the shapes in order

@@ -55,6 +55,10 @@ MUTANTS = [
     ("bounding box keeps the first tuple as the upper end",
      "if (found == 0 || v > out[2 * i + 1]) out[2 * i + 1] = v;", "if (found == 0) out[2 * i + 1] = v;",
      [lambda o: pins.test_nonzero_bbox_closed_forms(o)]),
+    ("product window reads x with y's bias",
+     "multiply_into(y, ybias + tuple_to_index(t.data(), yshape, dim), x,\n                  xbias + tuple_to_index",
+     "multiply_into(y, ybias + tuple_to_index(t.data(), yshape, dim), x,\n                  ybias + tuple_to_index",
+     [lambda o: pins.test_windows_both_sides_against_numpy_slicing(o, "f64", 1)]),
     ("bf16 product rounds with f16 parameters",
      "yy[iy] = uint16_t(round_to_format(exact, 8, -126, 127, 8));",
      "yy[iy] = uint16_t(round_to_format(exact, 11, -14, 15, 5));",

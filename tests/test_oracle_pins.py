@@ -658,3 +658,58 @@ def test_nonzero_bbox_storage_types(orc, dtype):
     ra, rb = conv(a), conv(b)
     want = _bbox_numpy([orc.to_f64(ra, dtype), orc.to_f64(rb, dtype)], [s1, s2])
     assert list(orc.nonzero_bbox([ra, rb], [s1, s2], dtype)) == want
+
+
+# ---------------------------------------------------------------- Section 4: windows on both sides
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("seed", range(4))
+def test_windows_both_sides_against_numpy_slicing(orc, dtype, seed):
+    rng = np.random.default_rng(500 + seed)
+    d = int(rng.integers(1, 5))
+    ext = [int(v) for v in rng.integers(0, 5, size=d)]
+    xs = [e + int(rng.integers(0, 4)) for e in ext]
+    ys = [e + int(rng.integers(0, 4)) for e in ext]
+    xo = [int(rng.integers(0, a - e + 1)) for a, e in zip(xs, ext)]
+    yo = [int(rng.integers(0, a - e + 1)) for a, e in zip(ys, ext)]
+    nx, ny = int(np.prod(xs)), int(np.prod(ys))
+    xv = rng.standard_normal(nx) + 2.0
+    yv = rng.standard_normal(ny) + 2.0
+    if dtype == "f64":
+        x, y = xv, yv
+    elif dtype == "f32":
+        x, y = xv.astype(np.float32), yv.astype(np.float32)
+    else:
+        x, y = orc.from_f64(xv, dtype), orc.from_f64(yv, dtype)
+    xw = tuple(slice(o, o + e) for o, e in zip(xo, ext))
+    yw = tuple(slice(o, o + e) for o, e in zip(yo, ext))
+    want = y.reshape(ys).copy()
+    want[yw] = x.reshape(xs)[xw]
+    got = orc.copy_views(ext, x, xs, xo, y, ys, yo, dtype)
+    assert got.tobytes() == want.reshape(-1).tobytes()
+    # product: numpy elementwise on f64/f32, the oracle's own scalar product elsewhere
+    got = orc.product_views(ext, x, xs, xo, y, ys, yo, dtype)
+    if dtype in ("f64", "f32"):
+        want = y.reshape(ys).copy()
+        want[yw] = want[yw] * x.reshape(xs)[xw]
+        assert got.tobytes() == want.reshape(-1).tobytes()
+    else:
+        sub = orc.product(x.reshape(xs)[xw].reshape(-1).copy(), ext, y.reshape(ys)[yw].reshape(-1).copy(), ext, dtype)
+        want = y.reshape(ys).copy()
+        want[yw] = sub.reshape(ext)
+        assert got.tobytes() == want.reshape(-1).tobytes()
+
+
+def test_windows_reduce_to_one_sided_views(orc):
+    # x's window at the origin with x's full extent is product_at / crop_at
+    xs, ys, st = (3, 4, 5), (6, 7, 9), (2, 1, 3)
+    x = synth_like(int(np.prod(xs)), 31)
+    y = synth_like(int(np.prod(ys)), 32)
+    assert orc.product_views(xs, x, xs, (0, 0, 0), y, ys, st, "f64").tobytes() == \
+        orc.product_at(x, xs, y, ys, st, "f64").tobytes()
+    x2 = orc.copy_views(xs, y, ys, st, np.zeros(int(np.prod(xs))), xs, (0, 0, 0), "f64")
+    assert x2.tobytes() == orc.crop_at(y, xs, ys, st, "f64").tobytes()
+
+
+def synth_like(n, seed):
+    return np.random.default_rng(seed).standard_normal(n)
