@@ -563,6 +563,19 @@ def run_extra_workloads(args, triot, synth, dev, stream):
     r["crop_at"] = op_entry(2 * 8 * 8 ** 6, ms, peak, 8 ** 6)
     res["fft_pad_f64_d6"] = r
     del xv, yv, xb
+    # two PMFs on one grid (Section 4's product over the intersecting support): x (16)^6 at
+    # the origin, y (16)^6 at (4)^6, y *= x over the shared (12)^6; 3 * 8 * 12^6 bytes,
+    # copies rotated so the touched data exceeds 4x L2
+    pm = (16,) * 6
+    ni = 12 ** 6
+    ncopy = int(4 * l2 // (3 * 8 * ni)) + 1
+    xp = [torch.from_numpy(synth.uniform01(1012, 16 ** 6).reshape(pm)).to(dev) for _ in range(ncopy)]
+    yp = [torch.from_numpy(synth.uniform01(1013, 16 ** 6).reshape(pm)).to(dev) for _ in range(ncopy)]
+    ms = time_op(lambda k, st: triot.triot_product_support(xp[k % ncopy], (0,) * 6, yp[k % ncopy], (4,) * 6,
+                                                           stream=st), 2 * ncopy, stream)
+    res["pmf_support_f64_d6"] = {"product_support": op_entry(3 * 8 * ni, ms, peak, ni), "copies_rotated": ncopy,
+                                 "intersection": [12] * 6}
+    del xp, yp
     torch.cuda.empty_cache()
     # moment of the product of the f64 d=8 pair (x 9^8, y (12,8)x4) over I = (9,8)x4, fused:
     # 2 * 8 * |I| bytes read, against 4 * 8 * |I| for the product followed by the moment

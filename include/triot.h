@@ -154,6 +154,31 @@ int triot_product_at(int rank, const int64_t* xshape, const void* x, const int64
                      const int64_t* ystart, int dtype, void* stream);
 
 /*
+ * Windows on both sides (Section 4: views over the intersecting support of two tensors, so
+ * that e.g. the product of two PMFs with different supports runs without copies).  `ext` is
+ * the window's extents; `xstart` / `ystart` (HOST arrays of rank non-negative starts) place
+ * it in the containers x (xshape) and y (yshape), each addressed with its own shape.
+ * triot_copy_views    -- y[ystart + t] = x[xstart + t] for every tuple t of ext (bit-exact).
+ * triot_product_views -- y[ystart + t] = y[ystart + t] * x[xstart + t] (rounded as
+ *   triot_product).
+ *   Both windows must lie inside their containers (TRIOT_ERR_SHAPE otherwise); x and y must
+ *   not overlap; the rest of y is untouched.
+ * triot_product_support -- the product of two tensors placed on a common integer grid:
+ *   x covers the tuples xorigin + [0, xshape), y covers yorigin + [0, yshape) (origins are
+ *   HOST arrays of rank signed values, |origin| < 2^62); y is multiplied by x over the
+ *   tuples both cover (none: nothing happens), i.e. triot_product_views on the window
+ *   [max(xorigin, yorigin), min(xorigin + xshape, yorigin + yshape)).
+ */
+int triot_copy_views(int rank, const int64_t* ext, const int64_t* xshape, const void* x,
+                     const int64_t* xstart, const int64_t* yshape, void* y, const int64_t* ystart,
+                     int dtype, void* stream);
+int triot_product_views(int rank, const int64_t* ext, const int64_t* xshape, const void* x,
+                        const int64_t* xstart, const int64_t* yshape, void* y, const int64_t* ystart,
+                        int dtype, void* stream);
+int triot_product_support(int rank, const int64_t* xshape, const void* x, const int64_t* xorigin,
+                          const int64_t* yshape, void* y, const int64_t* yorigin, int dtype, void* stream);
+
+/*
  * triot_moment_workspace_size -- bytes of device workspace triot_moment needs for this
  *   shape and dtype (per-block partial sums).  Writes *bytes; never fails for valid
  *   arguments.  The size depends only on (rank, shape, dtype) and the tuning in force.

@@ -4,6 +4,7 @@
 // kernels run unchanged on the view: strides from y's shape, y's pointer advanced by the bias.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <string>
 
@@ -110,6 +111,70 @@ int triot_embed_at(int rank, const int64_t* xshape, const void* x, const int64_t
   // y[ystart + t] = x[t]: the written view of y has x's extent (every tuple inside)
   return launch_rows(ROW_EMBED, rank, xshape, x, xshape, advance(y, bias, dtype), dtype,
                      TRIOT_EMBED_NOPAD, s, nullptr, nullptr, yshape);
+}
+
+// ---- windows on both sides (Section 4: views over the intersecting support of two tensors)
+
+namespace {
+int views_check(int rank, const int64_t* ext, const int64_t* xshape, const int64_t* xstart,
+                const int64_t* yshape, const int64_t* ystart, int64_t& xbias, int64_t& ybias) {
+  int st = window_bias(rank, ext, xshape, xstart, true, xbias);
+  if (st) return st;
+  return window_bias(rank, ext, yshape, ystart, true, ybias);
+}
+}  // namespace
+
+int triot_copy_views(int rank, const int64_t* ext, const int64_t* xshape, const void* x,
+                     const int64_t* xstart, const int64_t* yshape, void* y, const int64_t* ystart,
+                     int dtype, void* stream) {
+  if (!valid_dtype(dtype)) return fail(TRIOT_ERR_DTYPE, "unknown dtype code");
+  int64_t xb, yb;
+  int st = views_check(rank, ext, xshape, xstart, yshape, ystart, xb, yb);
+  if (st) return st;
+  const int64_t nx = count(rank, xshape), ny = count(rank, yshape), ne = count(rank, ext);
+  const int es = dtype_size(dtype);
+  if (ne == 0) return ok();
+  if (!x || !y) return fail(TRIOT_ERR_NULL, "x or y is NULL");
+  if (overlaps_bytes(x, size_t(nx) * es, y, size_t(ny) * es)) return fail(TRIOT_ERR_ALIAS, "x and y overlap");
+  // an embed of x's window into y's window with nothing to pad: every tuple is written
+  return launch_rows(ROW_EMBED, rank, ext, advance(x, xb, dtype), ext, advance(y, yb, dtype), dtype,
+                     TRIOT_EMBED_NOPAD, (cudaStream_t)stream, nullptr, xshape, yshape);
+}
+
+int triot_product_views(int rank, const int64_t* ext, const int64_t* xshape, const void* x,
+                        const int64_t* xstart, const int64_t* yshape, void* y, const int64_t* ystart,
+                        int dtype, void* stream) {
+  if (!valid_dtype(dtype)) return fail(TRIOT_ERR_DTYPE, "unknown dtype code");
+  int64_t xb, yb;
+  int st = views_check(rank, ext, xshape, xstart, yshape, ystart, xb, yb);
+  if (st) return st;
+  const int64_t nx = count(rank, xshape), ny = count(rank, yshape), ne = count(rank, ext);
+  const int es = dtype_size(dtype);
+  if (ne == 0) return ok();
+  if (!x || !y) return fail(TRIOT_ERR_NULL, "x or y is NULL");
+  if (overlaps_bytes(x, size_t(nx) * es, y, size_t(ny) * es)) return fail(TRIOT_ERR_ALIAS, "x and y overlap");
+  return launch_rows(ROW_PRODUCT, rank, ext, advance(x, xb, dtype), ext, advance(y, yb, dtype), dtype, 0,
+                     (cudaStream_t)stream, nullptr, xshape, yshape);
+}
+
+int triot_product_support(int rank, const int64_t* xshape, const void* x, const int64_t* xorigin,
+                          const int64_t* yshape, void* y, const int64_t* yorigin, int dtype, void* stream) {
+  if (rank < 1 || rank > kMaxRank) return fail(TRIOT_ERR_RANK, "rank outside [1, 24]");
+  if (!xshape || !yshape || !xorigin || !yorigin) return fail(TRIOT_ERR_NULL, "a shape or origin pointer is NULL");
+  int64_t ext[kMaxRank], xs[kMaxRank], ys[kMaxRank];
+  for (int i = 0; i < rank; ++i) {
+    if (xshape[i] < 0 || yshape[i] < 0) return fail(TRIOT_ERR_SHAPE, "negative extent");
+    const int64_t lim = int64_t(1) << 62;
+    if (xorigin[i] <= -lim || xorigin[i] >= lim || yorigin[i] <= -lim || yorigin[i] >= lim)
+      return fail(TRIOT_ERR_SHAPE, "origin outside (-2^62, 2^62)");
+    // the supports [origin, origin + shape) intersect in [lo, hi)
+    const int64_t lo = std::max(xorigin[i], yorigin[i]);
+    const int64_t hi = std::min(xorigin[i] + xshape[i], yorigin[i] + yshape[i]);
+    ext[i] = hi > lo ? hi - lo : 0;
+    xs[i] = hi > lo ? lo - xorigin[i] : 0;
+    ys[i] = hi > lo ? lo - yorigin[i] : 0;
+  }
+  return triot_product_views(rank, ext, xshape, x, xs, yshape, y, ys, dtype, stream);
 }
 
 }  // extern "C"

@@ -73,6 +73,9 @@ def lib() -> C.CDLL:
             "triot_embed_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, u, vp]),
             "triot_crop_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
             "triot_product_at": (i, [i, _I64P, vp, _I64P, vp, _I64P, i, vp]),
+            "triot_copy_views": (i, [i, _I64P, _I64P, vp, _I64P, _I64P, vp, _I64P, i, vp]),
+            "triot_product_views": (i, [i, _I64P, _I64P, vp, _I64P, _I64P, vp, _I64P, i, vp]),
+            "triot_product_support": (i, [i, _I64P, vp, _I64P, _I64P, vp, _I64P, i, vp]),
             "triot_moment_product_workspace_size": (i, [i, i, C.POINTER(_I64P), i, C.POINTER(sz)]),
             "triot_moment_product": (i, [i, i, C.POINTER(_I64P), C.POINTER(vp), i, vp, vp, sz, vp]),
             "triot_nonzero_bbox_workspace_size": (i, [i, i, C.POINTER(_I64P), i, C.POINTER(sz)]),
@@ -248,6 +251,27 @@ def triot_product_at(x: torch.Tensor, y: torch.Tensor, ystart, stream=None) -> t
     """y[ystart + t] *= x[t] over the tuples of x that fit in y."""
     _check(lib().triot_product_at(x.dim(), _shape(x.shape), _dev(x), _shape(y.shape), _dev(y), _shape(ystart),
                                   _dtype(x), _stream(stream)))
+    return y
+
+
+def triot_copy_views(ext, x: torch.Tensor, xstart, y: torch.Tensor, ystart, stream=None) -> torch.Tensor:
+    """y[ystart + t] = x[xstart + t] for every tuple t of ext (windows of two containers)."""
+    _check(lib().triot_copy_views(x.dim(), _shape(ext), _shape(x.shape), _dev(x), _shape(xstart),
+                                  _shape(y.shape), _dev(y), _shape(ystart), _dtype(x), _stream(stream)))
+    return y
+
+
+def triot_product_views(ext, x: torch.Tensor, xstart, y: torch.Tensor, ystart, stream=None) -> torch.Tensor:
+    """y[ystart + t] *= x[xstart + t] for every tuple t of ext (windows of two containers)."""
+    _check(lib().triot_product_views(x.dim(), _shape(ext), _shape(x.shape), _dev(x), _shape(xstart),
+                                     _shape(y.shape), _dev(y), _shape(ystart), _dtype(x), _stream(stream)))
+    return y
+
+
+def triot_product_support(x: torch.Tensor, xorigin, y: torch.Tensor, yorigin, stream=None) -> torch.Tensor:
+    """y *= x over the tuples both cover when x sits at xorigin and y at yorigin of one grid."""
+    _check(lib().triot_product_support(x.dim(), _shape(x.shape), _dev(x), _shape(xorigin), _shape(y.shape),
+                                       _dev(y), _shape(yorigin), _dtype(x), _stream(stream)))
     return y
 
 

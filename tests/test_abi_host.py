@@ -141,6 +141,20 @@ def test_bad_arguments_fail_before_any_gpu_work(tr):
     assert L.triot_moment_product(3, 2, neg, ptrs, 0, fake2, fake2, 1 << 20, None) == 2
     nbytes = C.c_size_t(0)
     assert L.triot_moment_product_workspace_size(3, 0, shp, 0, C.byref(nbytes)) == 8
+    # windows on both sides: each window inside its container; support origins bounded
+    e2 = tr._shape((2, 2))
+    assert L.triot_copy_views(2, e2, tr._shape((2, 3)), fake, tr._shape((1, 0)), tr._shape((4, 4)), fake2,
+                              tr._shape((0, 0)), 0, None) == 2
+    assert L.triot_product_views(2, e2, tr._shape((2, 3)), fake, tr._shape((0, 0)), tr._shape((4, 4)), fake2,
+                                 tr._shape((3, 0)), 0, None) == 2
+    assert L.triot_product_views(2, e2, tr._shape((2, 3)), fake, tr._shape((0, 0)), tr._shape((4, 4)), fake,
+                                 tr._shape((0, 0)), 0, None) == 6
+    assert L.triot_product_views(2, e2, tr._shape((2, 3)), fake, tr._shape((0, 0)), tr._shape((4, 4)), fake2,
+                                 tr._shape((0, 0)), 9, None) == 4
+    assert L.triot_product_support(2, tr._shape((2, 3)), fake, tr._shape((1 << 62, 0)), tr._shape((4, 4)), fake2,
+                                   tr._shape((0, 0)), 0, None) == 2
+    assert L.triot_product_support(2, tr._shape((2, 3)), fake, None, tr._shape((4, 4)), fake2,
+                                   tr._shape((0, 0)), 0, None) == 3
     # nonzero bounding box: tensor count, rank, dtype, shapes
     assert L.triot_nonzero_bbox(3, 0, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 8
     assert L.triot_nonzero_bbox(3, 5, shp, ptrs, 0, fake2, fake2, 1 << 20, None) == 8

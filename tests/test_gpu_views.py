@@ -103,3 +103,73 @@ def test_fft_pad_round_trip(tr):
     back = torch.empty(xs, dtype=torch.float64, device="cuda")
     tr.triot_crop_at(back, y, st)
     assert torch.equal(back, x)
+
+
+# ---------------------------------------------------------------- windows on both sides
+
+VIEWS2 = [
+    # ext, x container, x start, y container, y start
+    ((3, 4, 5), (6, 7, 9), (2, 1, 3), (5, 8, 7), (1, 4, 0)),
+    ((5, 9), (7, 10), (1, 1), (9, 13), (3, 2)),                     # odd starts: element paths
+    ((4, 16), (4, 32), (0, 8), (8, 48), (2, 16)),                   # aligned rows: vector paths
+    ((2, 3, 4, 5), (2, 3, 4, 5), (0, 0, 0, 0), (4, 6, 8, 10), (2, 3, 4, 5)),
+    ((1, 5000), (3, 6000), (2, 17), (2, 9000), (1, 3001)),          # a long row, segmented
+    ((0, 4), (3, 4), (1, 0), (2, 8), (0, 4)),                       # empty window
+    ((7, 1, 33), (9, 2, 40), (1, 1, 5), (8, 3, 35), (0, 2, 2)),     # a unit axis in the window
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", range(len(VIEWS2)))
+def test_copy_and_product_views_against_oracle(tr, dtype, case):
+    ext, xs, xo, ys, yo = VIEWS2[case]
+    xh = values(int(np.prod(xs)), dtype, 900 + case)
+    yh = values(int(np.prod(ys)), dtype, 950 + case)
+    band = 24
+    nyy = int(np.prod(ys))
+    buf = torch.full((nyy + 2 * band,), -9, dtype=TORCH[dtype], device="cuda")
+    y = buf[band:band + nyy].view(ys)
+    y.copy_(dev(yh, dtype, ys))
+    x = dev(xh, dtype, xs)
+    tr.triot_copy_views(ext, x, xo, y, yo)
+    want = orc.copy_views(ext, xh, xs, xo, yh, ys, yo, dtype)
+    assert host(y, dtype).tobytes() == want.tobytes()
+    tr.triot_product_views(ext, x, xo, y, yo)
+    want = orc.product_views(ext, xh, xs, xo, want, ys, yo, dtype)
+    assert host(y, dtype).tobytes() == want.tobytes()
+    sentinel = host(torch.full((1,), -9, dtype=TORCH[dtype], device="cuda"), dtype)[0]
+    hb = host(buf, dtype)
+    assert np.all(hb[:band] == sentinel) and np.all(hb[band + nyy:] == sentinel)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "bf16"])
+def test_product_support_of_two_pmfs(tr, dtype):
+    """Two PMFs on one integer grid with different supports: y *= x over the tuples both
+    cover, the rest of y untouched -- the oracle's window product on the intersection."""
+    xs, xo = (12, 9, 14), (-3, 5, 2)
+    ys, yo = (10, 12, 9), (1, 0, 6)
+    xh = values(int(np.prod(xs)), dtype, 61)
+    yh = values(int(np.prod(ys)), dtype, 62)
+    lo = [max(a, b) for a, b in zip(xo, yo)]
+    hi = [min(a + n, b + m) for a, n, b, m in zip(xo, xs, yo, ys)]
+    ext = [max(0, h - l) for l, h in zip(lo, hi)]
+    want = orc.product_views(ext, xh, xs, [l - a for l, a in zip(lo, xo)], yh, ys,
+                             [l - b for l, b in zip(lo, yo)], dtype)
+    y = dev(yh, dtype, ys)
+    tr.triot_product_support(dev(xh, dtype, xs), xo, y, yo)
+    assert host(y, dtype).tobytes() == want.tobytes()
+    # disjoint supports: nothing changes
+    y2 = dev(yh, dtype, ys)
+    tr.triot_product_support(dev(xh, dtype, xs), (100, 0, 0), y2, yo)
+    assert host(y2, dtype).tobytes() == yh.tobytes()
+
+
+def test_views_reject_bad_windows(tr):
+    x = torch.zeros((4, 5), device="cuda")
+    y = torch.zeros((6, 6), device="cuda")
+    with pytest.raises(tr.TriotError):
+        tr.triot_copy_views((3, 3), x, (2, 0), y, (0, 0))      # x window leaves x
+    with pytest.raises(tr.TriotError):
+        tr.triot_product_views((3, 3), x, (0, 0), y, (4, 0))   # y window leaves y
+    with pytest.raises(tr.TriotError):
+        tr.triot_product_views((2, 2), x, (0, 0), x, (1, 1))   # the same container
