@@ -6,14 +6,16 @@
 // The iteration runs over x's canonical shape (unit axes dropped, axes contiguous in all
 // three tensors merged).  A CTA takes a tile of whole rows (or one segment of a long row),
 // decodes each row's tuple once (Algorithm 4 with magic division) into the rows' offsets in
-// y and z (Horner with their strides), and then streams the tile element by element: x is
-// dense, so its index is the flat index.
+// y and z (Horner with their strides), and then streams the tile in slots of one 16-byte x
+// vector (or one element when x's rows are not whole vectors), two slots per thread in
+// flight: x is dense, so its index is the flat index.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <utility>
 
@@ -36,6 +38,7 @@ struct ApplyGeom {
   long long seg_len;
   long long ntiles;
   FastDiv Ldiv;               // divisor L (rows_per_tile > 1 only; L < 2^31)
+  int vec;                    // x elements per 16-byte access (1: element accesses)
 };
 
 namespace {
@@ -66,6 +69,64 @@ template <> struct Arith<__half> {
     return __float2half_rn(__fsub_rn(__fadd_rn(xf, __fmul_rn(yf, xf)), zf));
   }
 };
+
+template <typename T, int V>
+__device__ __forceinline__ void apply_slots(const ApplyGeom& g, T* __restrict__ x, const T* __restrict__ y,
+                                            const T* __restrict__ z, const long long* s_oy,
+                                            const long long* s_oz, long long xbase, long long col0,
+                                            long long nrows, long long E) {
+  const long long nslot = E / V;
+  auto slot_row = [&](long long sidx, long long& q, long long& c) {
+    const long long e = sidx * V;
+    if (nrows > 1) {
+      uint32_t cc;
+      q = fdivmod((uint32_t)e, g.Ldiv, cc);
+      c = cc;
+    } else {
+      q = 0;
+      c = e;
+    }
+  };
+  auto load_slot = [&](long long sidx, long long q, long long c, T (&xv)[V], T (&yv)[V], T (&zv)[V]) {
+    const long long xi = xbase + sidx * V;
+    const long long oy = s_oy[q] + (col0 + c) * g.syi, oz = s_oz[q] + (col0 + c) * g.szi;
+    if constexpr (V > 1) {
+      const uint4 w = __ldcs(reinterpret_cast<const uint4*>(x + xi));
+      memcpy(xv, &w, 16);
+    } else {
+      xv[0] = x[xi];
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      yv[i] = __ldg(y + oy + i * g.syi);
+      zv[i] = __ldg(z + oz + i * g.szi);
+    }
+  };
+  auto store_slot = [&](long long sidx, T (&xv)[V], const T (&yv)[V], const T (&zv)[V]) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) xv[i] = Arith<T>::run(xv[i], yv[i], zv[i]);
+    const long long xi = xbase + sidx * V;
+    if constexpr (V > 1) {
+      uint4 w;
+      memcpy(&w, xv, 16);
+      __stcs(reinterpret_cast<uint4*>(x + xi), w);
+    } else {
+      x[xi] = xv[0];
+    }
+  };
+  for (long long s0 = threadIdx.x; s0 < nslot; s0 += 2 * (long long)blockDim.x) {
+    const long long s1 = s0 + blockDim.x;
+    const bool two = s1 < nslot;
+    long long q0, c0, q1 = 0, c1 = 0;
+    slot_row(s0, q0, c0);
+    if (two) slot_row(s1, q1, c1);
+    T xa[V], ya[V], za[V], xb[V], yb[V], zb[V];
+    load_slot(s0, q0, c0, xa, ya, za);
+    if (two) load_slot(s1, q1, c1, xb, yb, zb);
+    store_slot(s0, xa, ya, za);
+    if (two) store_slot(s1, xb, yb, zb);
+  }
+}
 
 template <typename T, int NOUT>
 __global__ void __launch_bounds__(kApplyThreads) apply_kernel(const __grid_constant__ ApplyGeom g,
@@ -126,20 +187,13 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(const __grid_const
     }
     __syncthreads();
     const long long xbase = row0 * g.L + col0;
-    for (long long e = threadIdx.x; e < E; e += blockDim.x) {
-      long long q, c;
-      if (nrows > 1) {
-        uint32_t cc;
-        q = fdivmod((uint32_t)e, g.Ldiv, cc);
-        c = cc;
-      } else {
-        q = 0;
-        c = e;
-      }
-      const long long j = col0 + c;
-      const long long xi = xbase + e;
-      x[xi] = Arith<T>::run(x[xi], y[s_oy[q] + j * g.syi], z[s_oz[q] + j * g.szi]);
-    }
+    // slots of V consecutive x elements (V = 1, or one 16-byte vector when every row of x
+    // is a whole number of aligned vectors); y and z are read element by element.  Two
+    // slots per thread are loaded before either is computed, so six loads are in flight.
+    if (g.vec > 1)
+      apply_slots<T, 16 / sizeof(T)>(g, x, y, z, s_oy, s_oz, xbase, col0, nrows, E);
+    else
+      apply_slots<T, 1>(g, x, y, z, s_oy, s_oz, xbase, col0, nrows, E);
   }
 }
 
@@ -251,7 +305,15 @@ extern "C" int triot_apply(int op, int rank, const int64_t* xshape, void* x, con
     g.div[k] = make_fastdiv(ext[a] < 0xFFFFFFFFll ? (uint32_t)ext[a] : 1u);
   }
   g.rows32 = g.rows <= 0xFFFFFFFFll;
-  const long long target = 8192;
+  DeviceInfo dev;
+  int st = device_info(dev);
+  if (st) return st;
+  // x vectors when every row of x is a whole number of aligned 16-byte vectors
+  const int vw = 16 / es;
+  g.vec = ((reinterpret_cast<uintptr_t>(x) % 16) == 0 && g.L % vw == 0) ? vw : 1;
+  // tiles of up to 8192 elements, smaller for small problems so that every SM gets four
+  long long target = 8192;
+  target = std::max<long long>(256, std::min(target, (nx + 4ll * dev.sms - 1) / (4ll * dev.sms)));
   if (g.L <= target && g.L < (1ll << 31)) {
     g.rows_per_tile = std::max(1ll, std::min<long long>(kApplyTileRows, target / g.L));
     g.segs = 1;
@@ -261,13 +323,10 @@ extern "C" int triot_apply(int op, int rank, const int64_t* xshape, void* x, con
     if (g.rows_per_tile * g.L >= (1ll << 32)) return fail(TRIOT_ERR_ARG, "internal: tile too large");
   } else {
     g.rows_per_tile = 1;
-    g.seg_len = target;
-    g.segs = (g.L + target - 1) / target;
+    g.seg_len = (target + g.vec - 1) / g.vec * g.vec;  // segments start on a vector
+    g.segs = (g.L + g.seg_len - 1) / g.seg_len;
     g.ntiles = g.rows * g.segs;
   }
-  DeviceInfo dev;
-  int st = device_info(dev);
-  if (st) return st;
   const void* fn = apply_kernel_ptr(dtype, g.nouter);
   if (!fn) return fail(TRIOT_ERR_RANK, "no kernel for this effective rank");
   const long long grid = std::max(1ll, std::min<long long>(g.ntiles, (long long)dev.sms * 8));

@@ -7,7 +7,8 @@
 // and infinities count, +0 and -0 do not, and nothing is rounded).  The result per axis is
 // the least and greatest t_i over the counted tuples, and their number.
 //
-// Kernel: warps take rows of I (all axes but the innermost) in a strided order; a row's
+// Kernels: for rows of 32 elements or more, warps take rows of I (all axes but the
+// innermost) in a strided order; a row's
 // tuple is decoded once (Algorithm 4 with magic-number division) into each tensor's row
 // offset, and the lanes test the row's elements (coalesced along the innermost axis), each
 // lane keeping the least and greatest inner digit and a count.  A row with a counted
@@ -160,6 +161,117 @@ __global__ void __launch_bounds__(kBoxWarps * 32) bbox_kernel(const __grid_const
   }
 }
 
+// Short rows (fewer than 32 elements): a warp takes 32 consecutive rows at a time, one per
+// lane, so that each load instruction of the warp reads neighbouring rows (a contiguous
+// stretch of every tensor).  Each lane decodes its row (magic-number division) and tests the
+// row's elements; the outer axes' least and greatest digits over the group's counted rows
+// come from one warp min / max per axis, so the per-lane bookkeeping stays in registers.
+template <typename B, int N>
+__global__ void __launch_bounds__(kBoxWarps * 32) bbox_rows_kernel(const __grid_constant__ BoxGeom g,
+                                                                  long long* __restrict__ slots) {
+  __shared__ unsigned s_lo[kBoxWarps][kMaxRank], s_hi[kBoxWarps][kMaxRank];
+  __shared__ unsigned long long s_cnt[kBoxWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kBoxWarps + warp;
+  const long long W = (long long)gridDim.x * kBoxWarps;
+  const int D = g.D;  // >= 2 here (a short innermost axis and at least one outer axis)
+  unsigned lo[kMaxRank], hi[kMaxRank];  // outer axes (warp-uniform), registers
+#pragma unroll
+  for (int a = 0; a < kMaxRank; ++a) {
+    lo[a] = 0xFFFFFFFFu;
+    hi[a] = 0u;
+  }
+  unsigned ilo = 0xFFFFFFFFu, ihi = 0u;
+  unsigned long long cnt = 0;
+  const B* X[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) X[k] = static_cast<const B*>(g.x[k]);
+  const long long ngroups = (g.rows + 31) / 32;
+  for (long long grp = gw; grp < ngroups; grp += W) {
+    const long long r = grp * 32 + lane;
+    const bool valid = r < g.rows;
+    unsigned dig[kMaxRank];
+    long long off[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) off[k] = 0;
+    {
+      uint32_t q = valid ? (uint32_t)r : 0u;  // rows < 2^32 for this kernel
+#pragma unroll
+      for (int a = kMaxRank - 1; a >= 0; --a) {
+        dig[a] = 0;
+        if (a + 1 < D) {
+          uint32_t d = q;
+          if (a > 0) {
+            const uint32_t q1 = fdiv(q, g.div[a]);
+            d = q - q1 * g.div[a].d;
+            q = q1;
+          }
+          dig[a] = d;
+#pragma unroll
+          for (int k = 0; k < N; ++k) off[k] += (long long)d * g.stride[k][a];
+        }
+      }
+    }
+    unsigned rowcnt = 0;
+    if (valid) {
+      for (int j = 0; j < (int)g.L; ++j) {
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < N; ++k) all = all && nz_bits(__ldg(X[k] + off[k] + j * g.stride[k][D - 1]));
+        if (all) {
+          ilo = min(ilo, (unsigned)j);
+          ihi = max(ihi, (unsigned)j);
+          ++rowcnt;
+        }
+      }
+    }
+    cnt += rowcnt;
+    if (__any_sync(0xffffffffu, rowcnt != 0)) {
+#pragma unroll
+      for (int a = 0; a < kMaxRank; ++a) {
+        if (a + 1 >= D) break;
+        lo[a] = min(lo[a], __reduce_min_sync(0xffffffffu, rowcnt ? dig[a] : 0xFFFFFFFFu));
+        hi[a] = max(hi[a], __reduce_max_sync(0xffffffffu, rowcnt ? dig[a] : 0u));
+      }
+    }
+  }
+  ilo = __reduce_min_sync(0xffffffffu, ilo);
+  ihi = __reduce_max_sync(0xffffffffu, ihi);
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < kMaxRank; ++a) {
+      if (a + 1 >= D) break;
+      s_lo[warp][a] = lo[a];
+      s_hi[warp][a] = hi[a];
+    }
+    s_lo[warp][D - 1] = ilo;
+    s_hi[warp][D - 1] = ihi;
+    s_cnt[warp] = cnt;
+  }
+  __syncthreads();
+  long long* slot = slots + (long long)blockIdx.x * (2 * D + 1);
+  if (threadIdx.x < D) {
+    const int a = threadIdx.x;
+    unsigned l = 0xFFFFFFFFu, h = 0u;
+    unsigned long long c = 0;
+    for (int w = 0; w < kBoxWarps; ++w) {
+      if (s_cnt[w] == 0) continue;
+      l = min(l, s_lo[w][a]);
+      h = max(h, s_hi[w][a]);
+      c += s_cnt[w];
+    }
+    slot[2 * a] = c ? (long long)l : LLONG_MAX;
+    slot[2 * a + 1] = c ? (long long)h : -1;
+  }
+  if (threadIdx.x == 0) {
+    unsigned long long c = 0;
+    for (int w = 0; w < kBoxWarps; ++w) c += s_cnt[w];
+    slot[2 * D] = (long long)c;
+  }
+}
+
 // merge the CTAs' slots; write [lo_0, hi_0, .., count] in the caller's axis order (axes of
 // extent 1 in I: 0 .. 0 when anything counted); nothing counted: lo 0, hi -1 everywhere
 __global__ void __launch_bounds__(256) bbox_combine_kernel(const __grid_constant__ BoxGeom g, int nslots,
@@ -199,7 +311,15 @@ __global__ void __launch_bounds__(256) bbox_combine_kernel(const __grid_constant
 }
 
 template <typename B>
-const void* pick_bbox(int n) {
+const void* pick_bbox(int n, bool short_rows) {
+  if (short_rows) {
+    switch (n) {
+      case 1: return reinterpret_cast<const void*>(&bbox_rows_kernel<B, 1>);
+      case 2: return reinterpret_cast<const void*>(&bbox_rows_kernel<B, 2>);
+      case 3: return reinterpret_cast<const void*>(&bbox_rows_kernel<B, 3>);
+      default: return reinterpret_cast<const void*>(&bbox_rows_kernel<B, 4>);
+    }
+  }
   switch (n) {
     case 1: return reinterpret_cast<const void*>(&bbox_kernel<B, 1>);
     case 2: return reinterpret_cast<const void*>(&bbox_kernel<B, 2>);
@@ -214,6 +334,7 @@ struct BoxLaunch {
   BoxGeom g;
   int grid = 0;
   bool empty = false;
+  bool short_rows = false;
 };
 
 int plan_bbox(int rank, int n, const int64_t* const* shapes, int dtype, const void* const* ptrs, BoxLaunch& L) {
@@ -285,7 +406,10 @@ int plan_bbox(int rank, int n, const int64_t* const* shapes, int dtype, const vo
   DeviceInfo dev;
   int s = device_info(dev);
   if (s) return s;
-  const long long want = (g.rows + kBoxWarps - 1) / kBoxWarps;
+  // short rows: a warp per group of 32 rows; long rows: a warp per row
+  L.short_rows = g.D >= 2 && g.L < 32 && g.rows32;
+  const long long want = L.short_rows ? (g.rows + 32 * kBoxWarps - 1) / (32 * kBoxWarps)
+                                      : (g.rows + kBoxWarps - 1) / kBoxWarps;
   L.grid = L.empty ? 1 : (int)std::max(1ll, std::min(want, (long long)dev.sms * 8));
   return TRIOT_OK;
 }
@@ -328,9 +452,9 @@ int triot_nonzero_bbox(int rank, int ntensors, const int64_t* const* shapes, con
     nslots = 0;
   } else {
     const int es = dtype_size(dtype);
-    const void* fn = es == 8 ? pick_bbox<unsigned long long>(ntensors)
-                     : es == 4 ? pick_bbox<unsigned>(ntensors)
-                               : pick_bbox<unsigned short>(ntensors);
+    const void* fn = es == 8 ? pick_bbox<unsigned long long>(ntensors, L.short_rows)
+                     : es == 4 ? pick_bbox<unsigned>(ntensors, L.short_rows)
+                               : pick_bbox<unsigned short>(ntensors, L.short_rows);
     void* args[] = {(void*)&L.g, (void*)&slots};
     e = cudaLaunchKernel(fn, dim3(L.grid), dim3(kBoxWarps * 32), args, 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "bounding box kernel launch");
