@@ -154,12 +154,14 @@ int plan_moment_call(int rank, const int64_t* shape, int dtype, const void* p, c
     int occ = 1;
     if ((st = moment_occupancy(fmx, nw * 32, 0, 0, occ))) return st;
     const int cps = t.ctas_per_sm > 0 ? t.ctas_per_sm : occ;
-    // float storage: only large tensors whose rows can be read 16 bytes at a time (the
-    // per-CTA column pass and the row-side set-up need enough rows per warp to pay off;
-    // smaller tensors are latency-bound and the block kernels below serve them better)
-    const bool eligible = f64 || c.total >= kMx32MinElems;
+    // only large tensors (float storage also needs rows that can be read 16 bytes at a
+    // time; f64 a few rows per warp): the column pass and the row-side set-up at a warp's
+    // start and end need enough rows to pay off, and smaller tensors, which are
+    // latency-bound, are served better by the row and block kernels below
+    const bool eligible = c.total >= (f64 ? kMx64MinElems : kMx32MinElems);
     if (eligible && plan_moment_mx(c, rank, dtype_size(dtype), p, (long long)dev.sms * cps * nw, L) &&
-        (f64 || (L.mx.C * dtype_size(dtype)) % 16 == 0))
+        (f64 || (L.mx.C * dtype_size(dtype)) % 16 == 0) &&
+        (!f64 || L.mx.R >= kMxMinRowsPerWarp * L.mx.parts))
       return TRIOT_OK;
     L = MomentLaunch();
   }

@@ -214,14 +214,25 @@ __global__ void __launch_bounds__(kBoxWarps * 32) bbox_rows_kernel(const __grid_
     }
     unsigned rowcnt = 0;
     if (valid) {
-      for (int j = 0; j < (int)g.L; ++j) {
-        bool all = true;
+      // eight elements of every factor loaded before any is tested (no short-circuit: the
+      // loads of one batch are all in flight together)
+      for (int j0 = 0; j0 < (int)g.L; j0 += 8) {
+        B v[N][8];
 #pragma unroll
-        for (int k = 0; k < N; ++k) all = all && nz_bits(__ldg(X[k] + off[k] + j * g.stride[k][D - 1]));
-        if (all) {
-          ilo = min(ilo, (unsigned)j);
-          ihi = max(ihi, (unsigned)j);
-          ++rowcnt;
+        for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            v[k][jj] = j0 + jj < (int)g.L ? __ldg(X[k] + off[k] + (j0 + jj) * g.stride[k][D - 1]) : (B)0;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          bool all = j0 + jj < (int)g.L;
+#pragma unroll
+          for (int k = 0; k < N; ++k) all = all & nz_bits(v[k][jj]);
+          if (all) {
+            ilo = min(ilo, (unsigned)(j0 + jj));
+            ihi = max(ihi, (unsigned)(j0 + jj));
+            ++rowcnt;
+          }
         }
       }
     }

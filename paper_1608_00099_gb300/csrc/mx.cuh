@@ -10,6 +10,8 @@ constexpr int kMxMinCtas = 1;    // resident CTAs per SM the register budget is 
 constexpr int kMxJ = 8;          // columns per lane: a warp tile is 32 * kMxJ columns
 constexpr int kMxWindow = 1023;  // rows a lane sums in one fixed-point window (|c| < 2^53)
 constexpr int kMxMaxGrid = 16384;  // CTAs (partial vectors) of one launch at most
+constexpr long long kMx64MinElems = 1ll << 21;  // f64 tensors this large or larger
+constexpr int kMxMinRowsPerWarp = 4;            // and at least this many rows per warp
 
 struct MxGeom {
   int D;                         // effective rank

@@ -114,22 +114,6 @@ __device__ __forceinline__ RowInfo decode_row(const RowGeom& g, long long r) {
   return decode_row_impl<OP, NOUT, OP == ROW_PRODUCT || OP == ROW_EMBED_S>(g, r);
 }
 
-// element-level work of one op on one element, scalar
-template <int OP, typename T>
-__device__ __forceinline__ void row_elem(const RowGeom& g, T* __restrict__ A,
-                                         const T* __restrict__ B, const RowInfo& ri,
-                                         long long c) {
-  if constexpr ((OP == ROW_EMBED || OP == ROW_EMBED_S)) {
-    const bool in = ri.b >= 0 && c < g.b_inner;
-    if (in) A[ri.a + c] = B[ri.b + c];
-    else if (!g.nopad) A[ri.a + c] = T(0);
-  } else if constexpr (OP == ROW_CROP) {
-    A[ri.a + c] = B[ri.b + c];
-  } else {
-    A[ri.a + c] = mul_rn(A[ri.a + c], B[ri.b + c]);
-  }
-}
-
 // ------------------------------------------------------------------ the kernel
 //
 // Grid-stride loop over tiles.  Dynamic shared memory holds one RowInfo per row of a tile.
@@ -233,22 +217,47 @@ __global__ void __launch_bounds__(1024) rows_kernel(const __grid_constant__ RowG
         }
       }
     } else {
-      // Generic path: one element at a time (rows of any length, any alignment).
+      // Generic path: one element per slot (rows of any length, any alignment); the U
+      // slots' loads are all issued before any store, so they are in flight together.
       for (long long e0 = tid; e0 < E; e0 += (long long)nth * U) {
+        long long ia[U], ib[U];
+        bool ok[U], in[U];
+        T va[U], vb[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const long long e = e0 + (long long)u * nth;
-          if (e >= E) break;
-          long long q, c;
+          ok[u] = e < E;
+          long long q = 0, c;
           if (g.segs_per_row == 1) {
             uint32_t cc;
-            q = fdivmod((uint32_t)e, g.inner_div, cc);
+            q = fdivmod((uint32_t)(ok[u] ? e : 0), g.inner_div, cc);
             c = cc;
           } else {
-            q = 0;
-            c = col0 + e;
+            c = col0 + (ok[u] ? e : 0);
           }
-          row_elem<OP, T>(g, A, B, rinfo[q], c);
+          const RowInfo ri = rinfo[q];
+          ia[u] = ri.a + c;
+          ib[u] = ri.b + c;
+          in[u] = (OP == ROW_EMBED || OP == ROW_EMBED_S) ? (ri.b >= 0 && c < g.b_inner) : true;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          vb[u] = T(0);
+          if (ok[u] && in[u]) vb[u] = B[ib[u]];
+          if constexpr (OP == ROW_PRODUCT) {
+            if (ok[u]) va[u] = A[ia[u]];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (!ok[u]) continue;
+          if constexpr (OP == ROW_PRODUCT) {
+            A[ia[u]] = mul_rn(va[u], vb[u]);
+          } else if constexpr (OP == ROW_EMBED || OP == ROW_EMBED_S) {
+            if (in[u] || !g.nopad) A[ia[u]] = vb[u];  // vb is +0 outside x
+          } else {
+            A[ia[u]] = vb[u];
+          }
         }
       }
     }

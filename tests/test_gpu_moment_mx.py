@@ -28,16 +28,14 @@ def tr():
 
 
 MX_SHAPES = [
-    (9,) * 5,                    # one row axis, 26 tiles, the last partial
-    (9,) * 6,
-    (2,) * 20,                   # eight row axes of extent 2: carries at every depth
-    (3, 4, 5, 6, 7, 8),
-    (5, 3, 7, 2, 4096),
-    (7, 2, 3, 5, 2, 9, 40),
-    (3, 5000),                   # three rows
-    (1000, 1, 500),              # a unit axis between rows and columns
+    (9,) * 7,                    # 26 tiles of columns, the last partial
+    (2,) * 22,                   # many row axes of extent 2: carries at every depth
+    (5, 3, 7, 8, 4096),
+    (7, 4, 3, 5, 2, 9, 400),
+    (30, 100000),                # long rows, few of them
+    (5000, 1, 500),              # a unit axis between rows and columns
     (6, 4, 7, 3, 5, 6, 7, 3, 7, 3),
-    (11, 13, 128),
+    (110, 130, 256),
 ]
 
 
@@ -55,7 +53,7 @@ def test_mx_moment_against_oracle(tr, shape, law):
     assert tr.triot_moment(p).cpu().numpy().tobytes() == got.tobytes()
 
 
-@pytest.mark.parametrize("shape", [(9,) * 6, (2,) * 20, (5, 3, 7, 2, 4096)])
+@pytest.mark.parametrize("shape", [(9,) * 7, (2,) * 22, (5, 3, 7, 8, 4096)])
 def test_mx_point_masses_exact(tr, shape):
     n = int(np.prod(shape))
     for k in [0, 1, n // 3, n - 1]:
@@ -67,7 +65,7 @@ def test_mx_point_masses_exact(tr, shape):
 
 @pytest.mark.parametrize("case", ["wide", "subnormal_zero", "growing", "signed_growing", "tiny_only"])
 def test_mx_dynamic_range(tr, case):
-    shape = (40, 31, 17, 16)
+    shape = (40, 31, 170, 16)
     n = int(np.prod(shape))
     seeds = {"wide": 1, "subnormal_zero": 2, "growing": 3, "signed_growing": 4, "tiny_only": 5}
     rng = np.random.default_rng(seeds[case])
@@ -91,10 +89,10 @@ def test_mx_dynamic_range(tr, case):
 
 @pytest.mark.parametrize("where", ["first", "middle", "last_row", "partial_tile"])
 def test_mx_nonfinite_against_oracle(tr, where):
-    shape = (9, 9, 9, 9, 9)
+    shape = (9,) * 7
     n = int(np.prod(shape))
     v = synth.uniform01(77, n) - 0.25
-    k = {"first": 0, "middle": n // 2 + 13, "last_row": n - 100, "partial_tile": 6561 - 3}[where]
+    k = {"first": 0, "middle": n // 2 + 13, "last_row": n - 100, "partial_tile": 9 ** 4 - 3}[where]
     v[k] = np.inf
     v[(k + 4000) % n] = -np.inf if where == "middle" else np.nan
     ref = orc.moment(v, shape, "f64")
