@@ -214,7 +214,18 @@ int launch_moment(const MomentLaunch& L, int dtype, const void* p, double* out, 
   }
   const double* partc = static_cast<const double*>(ws);
   void* cargs[] = {(void*)&L.cg, (void*)&partc, (void*)&out};
-  e = cudaLaunchKernel(combine_kernel_ptr(), dim3(L.g.D + 1), dim3(kCombineThreadsHost), cargs, 0, stream);
+  // the combine as a programmatic dependent launch (it waits for the moment kernel itself)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.g.D + 1);
+  cfg.blockDim = dim3(kCombineThreadsHost);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = L.empty ? 0 : 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelExC(&cfg, combine_kernel_ptr(), cargs);
   if (e != cudaSuccess) return cuda_fail(e, "combine kernel launch");
   return ok();
 }

@@ -21,6 +21,10 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
   __shared__ unsigned s_emax[kCombineThreads / 32];
   __shared__ int s_bad[kCombineThreads / 32];
   __shared__ unsigned long long s_lo[kCombineThreads / 32], s_hi[kCombineThreads / 32];
+  // launched as a programmatic dependent of the moment kernel: its launch is prepared while
+  // that kernel runs, and this wait returns once the kernel has finished and its partials
+  // are visible (a plain launch returns at once)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int c = blockIdx.x;
   const int stride = g.D + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
