@@ -430,9 +430,10 @@ int triot_fastdiv_check(uint32_t d, const uint32_t* n, size_t count, uint32_t* q
  *   dtype under the tuning in force (no GPU work; needs the device's properties):
  *   *kernel = TRIOT_MK_ROWS (lane segments along the inner axis), TRIOT_MK_BLOCKS64 (f64
  *   block columns), TRIOT_MK_BLOCKS32 (float block columns), TRIOT_MK_WARPBLOCKS (float
- *   warp blocks) or TRIOT_MK_MARGINALS (f64 rows x columns split), *grid = its CTAs (the
- *   partial vectors the combine adds), and for TRIOT_MK_MARGINALS *rows / *cols the matrix
- *   view (else 0).  Any output pointer may be NULL.
+ *   warp blocks) or TRIOT_MK_MARGINALS (rows x columns split: f64 tensors of at least 2^21
+ *   elements, float tensors of at least 2^25 with 16-byte column runs), *grid = its CTAs
+ *   (the partial vectors the combine adds), and for TRIOT_MK_MARGINALS *rows / *cols the
+ *   matrix view (else 0).  Any output pointer may be NULL.
  */
 #define TRIOT_MK_ROWS 0
 #define TRIOT_MK_BLOCKS64 1
