@@ -755,6 +755,18 @@ def profile_op(args):
                          + 2, dtype=torch.float64, device=dev)
         for _ in range(n):
             triot.triot_moment_product([x8, y8], out=out, workspace=ws)
+    elif args.profile_op == "bbox_f64_d8":
+        # the bounding box workload: x 9^8 and y (12,8)x4 with 99.9 % zeros, over (9,8)x4
+        c8 = synth.config_f64_d8()
+        yh = c8.yprod_values()
+        yh[synth.uniform01(4242, yh.size) < 0.999] = 0.0
+        x8 = torch.from_numpy(c8.x_values().reshape(c8.xshape)).to(dev)
+        y8 = torch.from_numpy(yh.reshape(c8.prod_shape)).to(dev)
+        out = torch.empty(2 * len(c8.xshape) + 1, dtype=torch.int64, device=dev)
+        ws = torch.empty(triot.triot_nonzero_bbox_workspace_size([c8.xshape, c8.prod_shape], torch.float64) // 8
+                         + 2, dtype=torch.int64, device=dev)
+        for _ in range(n):
+            triot.triot_nonzero_bbox([x8, y8], out=out, workspace=ws)
     else:
         if args.profile_op == "moment_f64_d8":
             # the f64 d=8 step's moment: p = x / sum(x), x of shape 9^8, U(0,1)
@@ -795,7 +807,8 @@ def main():
     ap.add_argument("--autotune", default="", help="autotune the three ops and save the cache here")
     ap.add_argument("--no-tune-file", action="store_true", help="ignore the committed tuning file")
     ap.add_argument("--profile-op", default="",
-                    choices=["", "moment_product_f64_d8", "moment_f64_d8", "moment_f32_d24", "moment_bf16_blocks16"],
+                    choices=["", "moment_product_f64_d8", "moment_f64_d8", "moment_f32_d24", "moment_bf16_blocks16",
+                             "bbox_f64_d8"],
                     help="only run one op a few times (the command the ncu summaries capture)")
     args = ap.parse_args()
     if args.profile_op:
