@@ -374,12 +374,14 @@ __global__ void __launch_bounds__(kBoxWarps * 32, box_rows_ctas(N)) bbox_rows_ke
 
 // merge the CTAs' slots; write [lo_0, hi_0, .., count] in the caller's axis order (axes of
 // extent 1 in I: 0 .. 0 when anything counted); nothing counted: lo 0, hi -1 everywhere
-__global__ void __launch_bounds__(256) bbox_combine_kernel(const __grid_constant__ BoxGeom g, int nslots,
+constexpr int kBoxCombineWarps = 32;
+
+__global__ void __launch_bounds__(kBoxCombineWarps * 32) bbox_combine_kernel(const __grid_constant__ BoxGeom g, int nslots,
                                                            const long long* __restrict__ slots,
                                                            long long* __restrict__ out) {
-  // warp w reads slots w, w + 8, ..; lane c keeps component c (and c + 32) of a slot, whose
+  // warp w reads slots w, w + NW, ..; lane c keeps component c (and c + 32) of a slot, whose
   // 2D + 1 values are contiguous: [lo_0, hi_0, .., lo_{D-1}, hi_{D-1}, count]
-  constexpr int NW = 8;
+  constexpr int NW = kBoxCombineWarps;
   __shared__ long long s_part[NW][2 * kMaxRank + 1];
   __shared__ long long s_lo[kMaxRank], s_hi[kMaxRank];
   __shared__ unsigned long long s_cnt;
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(256) bbox_combine_kernel(const __grid_constant
   auto fold = [&](int c, long long acc, long long v) -> long long {
     return c == 2 * D ? acc + v : ((c & 1) ? max(acc, v) : min(acc, v));
   };
-  constexpr int U = 16;  // slots a warp has in flight
+  constexpr int U = 8;  // slots a warp has in flight
   long long a0 = init(lane), a1 = init(lane + 32);
   for (int k0 = warp; k0 < nslots; k0 += NW * U) {
     long long v0[U], v1[U];
@@ -601,7 +603,8 @@ int triot_nonzero_bbox(int rank, int ntensors, const int64_t* const* shapes, con
   }
   const long long* cslots = slots;
   void* cargs[] = {(void*)&L.g, (void*)&nslots, (void*)&cslots, (void*)&out};
-  e = cudaLaunchKernel(reinterpret_cast<const void*>(&bbox_combine_kernel), dim3(1), dim3(256), cargs, 0, s);
+  e = cudaLaunchKernel(reinterpret_cast<const void*>(&bbox_combine_kernel), dim3(1), dim3(kBoxCombineWarps * 32),
+                       cargs, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "bounding box combine launch");
   return ok();
 }
