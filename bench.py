@@ -755,6 +755,17 @@ def profile_op(args):
                          + 2, dtype=torch.float64, device=dev)
         for _ in range(n):
             triot.triot_moment_product([x8, y8], out=out, workspace=ws)
+    elif args.profile_op == "moment_product_bf16_d10":
+        # the precision workload's fused crop -> product -> moment: p (pshape) and q (qshape)
+        # in bf16, the moment of p * q over their intersection (rows of 3 elements)
+        pc = synth.config_precision()
+        P = synth.to_storage(pc.p64, "bf16").reshape(pc.pshape).to(dev)
+        Q = synth.to_storage(pc.q64, "bf16").reshape(pc.qshape).to(dev)
+        out = torch.empty(len(pc.pshape) + 1, dtype=torch.float64, device=dev)
+        ws = torch.empty(triot.triot_moment_product_workspace_size([pc.pshape, pc.qshape], torch.bfloat16) // 8
+                         + 2, dtype=torch.float64, device=dev)
+        for _ in range(n):
+            triot.triot_moment_product([P, Q], out=out, workspace=ws)
     elif args.profile_op == "bbox_f64_d8":
         # the bounding box workload: x 9^8 and y (12,8)x4 with 99.9 % zeros, over (9,8)x4
         c8 = synth.config_f64_d8()
@@ -808,7 +819,7 @@ def main():
     ap.add_argument("--no-tune-file", action="store_true", help="ignore the committed tuning file")
     ap.add_argument("--profile-op", default="",
                     choices=["", "moment_product_f64_d8", "moment_f64_d8", "moment_f32_d24", "moment_bf16_blocks16",
-                             "bbox_f64_d8"],
+                             "bbox_f64_d8", "moment_product_bf16_d10"],
                     help="only run one op a few times (the command the ncu summaries capture)")
     args = ap.parse_args()
     if args.profile_op:

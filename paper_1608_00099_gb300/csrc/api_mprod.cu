@@ -12,16 +12,19 @@
 #include "../../include/triot.h"
 #include "internal.h"
 #include "kernels.h"
+#include "mprod_rows.h"
 
 namespace triot {
 namespace {
 
 struct MProdLaunch {
   MProdGeom g;
+  MPRowsGeom rg;  // the short-row kernel's tiles
   CombineGeom cg;
   int grid = 0;
   size_t smem = 0;
   bool empty = false;
+  bool rows = false;  // the short-row kernel (moment_prod_rows.cu)
 };
 
 bool mul_overflows(int64_t a, int64_t b) { return a != 0 && b > INT64_MAX / a; }
@@ -138,6 +141,25 @@ int plan_mprod(int rank, int n, const int64_t* const* shapes, int dtype, const v
   DeviceInfo dev;
   int s = device_info(dev);
   if (s) return s;
+  // rows shorter than kMPRowsMaxL: CTA tiles of rows, streamed with a fixed column per thread
+  if (D >= 2 && g.L < kMPRowsMaxL && g.nrows < (int64_t(1) << 31)) {
+    const void* fr = moment_prod_rows_kernel_ptr(dtype, n);
+    if (!fr) return fail(TRIOT_ERR_ARG, "no kernel for this dtype and tensor count");
+    L.rows = true;
+    MPRowsGeom& rg = L.rg;
+    rg.rp = (kMPRowsWarps * 32) / (int)g.L;
+    rg.tile_rows = rg.rp * std::max(1, std::min(kMPRowsTileElems / (rg.rp * (int)g.L), kMPRowsTileRows / rg.rp));
+    rg.ldiv = make_fastdiv((uint32_t)g.L);
+    int occ = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fr, kMPRowsWarps * 32, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    const long long ntiles = (g.nrows + rg.tile_rows - 1) / rg.tile_rows;
+    L.grid = (int)std::max(1ll, std::min(ntiles, (long long)dev.sms * std::max(1, occ)));
+    L.smem = 0;
+    cg.nparts = L.grid;
+    if (L.grid > kMaxMomentParts) return fail(TRIOT_ERR_ARG, "grid exceeds the partial limit");
+    return TRIOT_OK;
+  }
   const void* fn = moment_prod_kernel_ptr(dtype, n);
   if (!fn) return fail(TRIOT_ERR_ARG, "no kernel for this dtype and tensor count");
   L.smem = (size_t)mprod_dyn_smem(D - 1);
@@ -196,14 +218,32 @@ int triot_moment_product(int rank, int ntensors, const int64_t* const* shapes, c
   cudaError_t e;
   double* part = static_cast<double*>(workspace);
   if (!L.empty) {
-    const void* fn = moment_prod_kernel_ptr(dtype, ntensors);
-    void* args[] = {(void*)&L.g, (void*)&part};
-    e = cudaLaunchKernel(fn, dim3(L.grid), dim3(kMProdWarps * 32), args, L.smem, s);
+    if (L.rows) {
+      void* args[] = {(void*)&L.g, (void*)&L.rg, (void*)&part};
+      e = cudaLaunchKernel(moment_prod_rows_kernel_ptr(dtype, ntensors), dim3(L.grid), dim3(kMPRowsWarps * 32), args,
+                           0, s);
+    } else {
+      void* args[] = {(void*)&L.g, (void*)&part};
+      e = cudaLaunchKernel(moment_prod_kernel_ptr(dtype, ntensors), dim3(L.grid), dim3(kMProdWarps * 32), args,
+                           L.smem, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "moment-product kernel launch");
   }
+  // the combine is a programmatic dependent of the kernel: its launch overlaps the kernel's
+  // tail and its first instruction waits for the kernel's completion
   const double* partc = part;
   void* cargs[] = {(void*)&L.cg, (void*)&partc, (void*)&out};
-  e = cudaLaunchKernel(combine_kernel_ptr(), dim3(L.g.D + 1), dim3(kCombineThreadsHost), cargs, 0, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.g.D + 1);
+  cfg.blockDim = dim3(kCombineThreadsHost);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = L.empty ? 0 : 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelExC(&cfg, combine_kernel_ptr(), cargs);
   if (e != cudaSuccess) return cuda_fail(e, "combine kernel launch");
   return ok();
 }

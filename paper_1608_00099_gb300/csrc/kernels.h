@@ -28,4 +28,6 @@ const void* moment_mx64_kernel_ptr();
 const void* moment_mx32_kernel_ptr(int dtype, int V);
 // moment of a product of tensors: one kernel per dtype and tensor count (1..4)
 const void* moment_prod_kernel_ptr(int dtype, int ntensors);
+// the same on rows shorter than kMPRowsMaxL elements (CTA tiles of rows, mprod_rows.h)
+const void* moment_prod_rows_kernel_ptr(int dtype, int ntensors);
 }  // namespace triot

@@ -125,3 +125,53 @@ def test_moment_product_point_mass_exact_and_deterministic(tr):
     a = tr.triot_moment_product(ts).cpu().numpy()
     b = tr.triot_moment_product(ts).cpu().numpy()
     assert a.tobytes() == b.tobytes()
+
+
+# rows of I shorter than 8 elements take the tiled short-row kernel: several tiles and a
+# partial last one, strided row axes, two to four factors, every dtype
+SHORT = [
+    [(300, 41, 2), (301, 40, 3)],
+    [(9, 8, 9, 8, 9, 4), (9, 9, 9, 9, 9, 5)],
+    [(64, 33, 7), (65, 32, 7), (64, 32, 8)],
+    [(40, 1, 30, 5), (41, 3, 30, 6), (40, 2, 31, 5), (42, 1, 30, 5)],
+    [(5000, 3, 1), (5001, 4, 2)],
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", range(len(SHORT)))
+def test_moment_product_short_rows(tr, dtype, case):
+    shapes = SHORT[case]
+    xs = [values(int(np.prod(s)), dtype, 900 + 10 * case + k) for k, s in enumerate(shapes)]
+    check(tr, xs, shapes, dtype)
+
+
+@pytest.mark.parametrize("where", ["first", "last"])
+def test_moment_product_short_rows_wide_range_and_specials(tr, where):
+    rng = np.random.default_rng(62)
+    shapes = [(60, 50, 3), (61, 50, 4)]
+    xs = [rng.standard_normal(int(np.prod(s))) * 10.0 ** rng.integers(-150, 150, size=int(np.prod(s)))
+          for s in shapes]
+    xs[0][:40] = rng.standard_normal(40) * 1e-310
+    xs[1][50:70] = 0.0
+    check(tr, xs, shapes, "f64")
+    t = (5, 7, 2) if where == "first" else (59, 49, 1)
+    xs[0][t[0] * 150 + t[1] * 3 + t[2]] = np.inf
+    xs[1][t[0] * 200 + t[1] * 4 + t[2]] = 2.0     # y at the same tuple: finite and nonzero
+    if where == "last":
+        xs[0][(t[0] // 2) * 150 + 3 * 3 + 0] = np.nan   # tuple (29, 3, 0), in another tile
+    got = tr.triot_moment_product([dev(x, "f64", s) for x, s in zip(xs, shapes)]).cpu().numpy()
+    ref = orc.moment_product(xs, shapes, "f64")
+    for g_, r_ in zip(got, ref):
+        assert (np.isnan(g_) and np.isnan(r_)) or g_ == r_, (got, ref)
+
+
+def test_moment_product_short_rows_point_masses_exact(tr):
+    shapes = [(33, 17, 5), (34, 17, 6)]
+    for t in [(0, 0, 0), (32, 16, 4), (17, 3, 2)]:
+        x = torch.zeros(shapes[0], dtype=torch.float32, device="cuda")
+        y = torch.zeros(shapes[1], dtype=torch.float32, device="cuda")
+        x[t] = 0.75
+        y[t] = 2.0
+        got = tr.triot_moment_product([x, y]).cpu().numpy()
+        assert list(got) == [1.5 * v for v in t] + [1.5]
