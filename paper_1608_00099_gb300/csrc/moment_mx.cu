@@ -122,12 +122,23 @@ __device__ __noinline__ void mx_end_window(const MxGeom& g, MxCold<J>& st, __int
     }
     st.Ad[s - 1] += fixed_to_double(S1, sc);
     st.Ad[D] += fixed_to_double(st.Mtot, sc);
-    for (int a = s; a < D; ++a) {
-      __int128 acc = 0;
-      for (int j = 0; j < J; ++j)
-        if (colok >> j & 1u) mac64x32(acc, st.cs[j], mx_col_digit(g, (uint32_t)(cbase + 32 * j), a));
-      st.Ad[a] += fixed_to_double(acc, sc);
+    // column axes: each of the lane's columns decoded once into all its digits
+    __int128 acc[kMaxRank];
+    for (int a = s; a < D; ++a) acc[a] = 0;
+    for (int j = 0; j < J; ++j) {
+      if (!(colok >> j & 1u)) continue;
+      uint32_t c = (uint32_t)(cbase + 32 * j);
+      for (int a = D - 1; a >= s; --a) {
+        uint32_t d = c;
+        if (a > s) {
+          const uint32_t q = fdiv(c, g.div[a]);
+          d = c - q * g.div[a].d;
+          c = q;
+        }
+        mac64x32(acc[a], st.cs[j], d);
+      }
     }
+    for (int a = s; a < D; ++a) st.Ad[a] += fixed_to_double(acc[a], sc);
   }
   st.Mtot = 0;
 }
