@@ -53,12 +53,6 @@ __device__ __forceinline__ void cf_mac(CF& a, const CF& b, uint32_t t) {  // a +
   a.l += fmaf(b.h, tf, -p) + b.l * tf;
 }
 
-// digit of column `col` on column axis a (s <= a < D)
-__device__ __forceinline__ uint32_t mx32_col_digit(const MxGeom& g, uint32_t col, int a) {
-  for (int b = g.D - 1; b > a; --b) col = fdiv(col, g.div[b]);
-  return a == g.s ? col : col - fdiv(col, g.div[a]) * g.div[a].d;
-}
-
 // the lane's cold state (local memory): the row levels above the eager axes, and totals
 struct Mx32Cold {
   CF Aa[kMaxRank];         // row axes 0 .. s-1-kEager: sums of mass * digit
