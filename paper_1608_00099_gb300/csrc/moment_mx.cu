@@ -6,7 +6,7 @@
 // column axis a,  m_a = sum over columns c of  t_a(c) * (mass of column c).  Each warp owns
 // one tile of 32*J columns (lane l holds columns l, l + 32, ..., l + 32(J-1) of the tile)
 // and a contiguous range of rows.  Rows are read straight from HBM with coalesced loads
-// (the warp reads 32 x J x 8 contiguous bytes of a row), two rows ahead of the one being
+// (the warp reads 32 x J x 8 contiguous bytes of a row), three rows ahead of the one being
 // summed; every element costs one load, its conversion to fixed point and two integer
 // adds: one into its column's sum, one into the lane's part of the row's mass.  The row's
 // digits are the same for the whole warp and advance like Algorithm 3 (one increment per
@@ -285,8 +285,8 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
     EW = 0;
   };
 
-  // ---- rows: loads straight from HBM into a ring of three row buffers, so that while one
-  // row is summed the next two are in flight (2 x 32 x J x 8 bytes per warp)
+  // ---- rows: loads straight from HBM into a ring of four row buffers, so that while one
+  // row is summed the next three are in flight (3 x 32 x J x 8 bytes per warp)
   const unsigned long long* prow =
       reinterpret_cast<const unsigned long long*>(p) + (r0 * g.C + cbase);  // slot 0, row r0
   auto load = [&](unsigned long long (&v)[J], long long r) {
@@ -372,18 +372,22 @@ __global__ void __launch_bounds__(kMxWarps * 32, kMxMinCtas) moment_mx64_kernel(
     }
   };
   if (r1 > r0) {
-    unsigned long long va[J], vb[J], vc[J];
+    unsigned long long va[J], vb[J], vc[J], vd[J];
     load(va, r0);
     if (r0 + 1 < r1) load(vb, r0 + 1);
-    for (long long r = r0; r < r1; r += 3) {
-      if (r + 2 < r1) load(vc, r + 2);
+    if (r0 + 2 < r1) load(vc, r0 + 2);
+    for (long long r = r0; r < r1; r += 4) {
+      if (r + 3 < r1) load(vd, r + 3);
       row(va);
       if (r + 1 >= r1) break;
-      if (r + 3 < r1) load(va, r + 3);
+      if (r + 4 < r1) load(va, r + 4);
       row(vb);
       if (r + 2 >= r1) break;
-      if (r + 4 < r1) load(vb, r + 4);
+      if (r + 5 < r1) load(vb, r + 5);
       row(vc);
+      if (r + 3 >= r1) break;
+      if (r + 6 < r1) load(vc, r + 6);
+      row(vd);
     }
     end_window();
   }
