@@ -257,7 +257,10 @@ int triot_moment_product_workspace_size(int rank, int ntensors, const int64_t* c
  *   workspace: device scratch of at least triot_moment_product_workspace_size() bytes,
  *   16-byte aligned.  Sums are fixed point, exact within windows of at most 1024 elements
  *   per thread (error at most 2^-52 times the window's largest |w| per element for f64
- *   tensors, 2^-48 for the others); partials are combined independently of their order.
+ *   tensors, 2^-48 for the others); when the last axis of I is shorter than 8 (a CTA-tiled
+ *   kernel), relative to the largest |w| the CTA has met so far (at most 2^-52 of it per
+ *   element, every dtype).  Partials are combined independently of their order, and a
+ *   non-finite weight propagates as in a plain sum.  Two kernels are enqueued.
  *   Errors: TRIOT_ERR_ARG (ntensors outside 1..4), TRIOT_ERR_RANK, TRIOT_ERR_SHAPE
  *   (negative extent, extent >= 2^31), TRIOT_ERR_NULL, TRIOT_ERR_DTYPE,
  *   TRIOT_ERR_WORKSPACE, TRIOT_ERR_CUDA.  An empty intersection writes zeros.
