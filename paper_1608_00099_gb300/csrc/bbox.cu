@@ -174,9 +174,9 @@ __global__ void __launch_bounds__(kBoxWarps * 32) bbox_kernel(const __grid_const
 // division) into shared memory; (2) the tile's elements are tested, kBoxU per thread in
 // flight, each counted element flagging its row; (3) the flagged rows' digits are decoded
 // and the outer axes' least and greatest digits merged with one warp min / max per axis
-// (lane a of every warp keeps axis a's running values).  Step (3) of a tile runs together
-// with step (1) of the next, on the same rows of the same threads, so a tile costs two
-// barriers.
+// (lane a of every warp keeps axis a's running values).  Two buffers of row offsets and
+// flags: while a tile streams (2), step (3) of the CTA's previous tile and step (1) of its
+// next run between the tile's first loads and their use, so a tile costs one barrier.
 constexpr int kBoxU = 4;
 constexpr int kBoxTileElems = 4096;  // elements of a short-row tile (at most kBoxTileRows rows)
 constexpr int kBoxTileRows = 512;
@@ -187,8 +187,8 @@ constexpr int kBoxTableEntries = 1024;  // P * N offsets of the split decode
 __host__ __device__ constexpr int box_rows_ctas(int n) { return n <= 2 ? 8 : (n == 3 ? 6 : 5); }
 
 template <typename B, int N>
-__global__ void __launch_bounds__(kBoxWarps * 32, box_rows_ctas(N)) bbox_rows_kernel(const __grid_constant__ BoxGeom g,
-                                                                  long long* __restrict__ slots) {
+__global__ void __launch_bounds__(kBoxWarps * 32, box_rows_ctas(N))
+    bbox_rows_kernel(const __grid_constant__ BoxGeom g, long long* __restrict__ slots) {
   __shared__ unsigned s_lo[kBoxWarps][kMaxRank], s_hi[kBoxWarps][kMaxRank];
   __shared__ unsigned long long s_cnt[kBoxWarps];
   __shared__ long long s_off[2][N][kBoxTileRows];  // two tiles: one streams, the next is decoded
